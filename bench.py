@@ -1,0 +1,303 @@
+"""Benchmark: stationary pmfs per second at N = 2000 bins, each within 1e-6 L1
+of the FP64 oracle.
+
+Workload (one step): the 256 x 256 pixel array (65536 pixels, N = 2000,
+t_r = 100 ns, t_d = 75 ns, tau ~ U[5,95] ns, sigma ~ U[0.2,1] ns,
+S, B ~ logU[0.01,5], seed 5).  A step runs the whole path through the C ABI:
+dead-time shift (host), FP64 cumulative flux, row sums and matrix-free power
+iteration of every pixel to the 1e-6 stop rule, in one persistent launch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  The reference arm times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stationary PDFs/sec at N=2000, 1e-6 L1 vs FP64 oracle (learned+batched vs plain)"
+UNIT = "PDFs/s"
+TOL = 1e-6
+MAX_ITER = 1000
+WORKLOAD = "array256: 256x256 pixels, N=2000, t_r=100ns, t_d=75ns, tau~U[5,95], sigma~U[0.2,1], S,B~logU[0.01,5], seed 5"
+SM_COUNT = 152
+FP32_LANES = 128           # FP32 FMA lanes per SM
+SM_MAX_MHZ = 2070.0        # maximum SM clock
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [x for x in sm if smax and x > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle (reference arm, cpu_baseline)
+
+def oracle_rate(px_sample, nthreads):
+    import oracle
+    pix = [dict(zip(px_sample.dtype.names, (v.item() for v in rec))) for rec in px_sample]
+    t0 = time.perf_counter()
+    _, _, iters, used = oracle.batch_stationary(pix, tol=1e-12, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return len(pix) / dt, dt, used
+
+
+def cpu_sample(px, n):
+    from paper_2509_20500_gb300 import workloads as W
+    idx = W.sample_indices(len(px), n, seed=55)
+    return px[idx], idx
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2509_20500_gb300 import workloads as W
+    px = W.array256()
+    cores = os.cpu_count() or 1
+    per_step = args.ref_sample
+    sample, _ = cpu_sample(px, per_step * (args.steps + args.warmup))
+    times = []
+    for s in range(args.warmup + args.steps):
+        chunk = sample[s * per_step:(s + 1) * per_step]
+        rate, dt, used = oracle_rate(chunk, cores)
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step_sample_pixels": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{per_step} pixels per step drawn by seed 55 from the 65536-pixel array; "
+                                   "sequential FP64 construction + dense power iteration to 1e-12"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def flush_l2(buf):
+    buf.add_(1.0)       # writes 256 MiB (> 129 MB L2)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2509_20500_gb300 import build, spl, workloads as W
+    build.build()
+    L = spl.lib()
+
+    # each rank owns an independent 65536-pixel array (weak scaling, no collective)
+    px = W.array256(seed=5 + rank)
+    n = len(px)
+    off = spl.offsets_of(px)
+    total = int(off[-1])
+    out = torch.empty(total, dtype=torch.float32, device=dev)
+    d_off = torch.from_numpy(off).to(dev)
+    c_px = spl.pixels_to_c(px)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(time_kernel=False, reports=False):
+        return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
+                                    c_pixels=c_px, time_kernel=time_kernel)
+
+    # untimed: per-pixel iteration counts for the algorithmic work (deterministic)
+    _, _, reps = step(reports=True)
+    assert np.all(reps["status"] == 0), "some pixels did not converge"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    for k in range(args.steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        step(time_kernel=True)
+        ev[k][1].record(stream)
+        kern_ms.append(spl.batch_kernel_ms())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    # roofline of the dominant kernel: the persistent matrix-free batch kernel.
+    # Algorithmic work: every pixel runs one dense row pass and `iters` dense
+    # column passes over its N x N regenerated matrix, one FFMA (2 FLOP) per entry.
+    N2 = px["n_bins"].astype(np.float64) ** 2
+    flop = float(2.0 * np.sum(N2 * (1 + reps["iters"])))
+    kms = statistics.median(kern_ms)
+    achieved = flop / (kms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    # end to end through the host-buffer entry point (H2D of the pixel list,
+    # D2H of every pmf and report inside the timed region)
+    h_out = np.empty(total, dtype=np.float32)
+    try:
+        import ctypes
+        h_out_pinned = torch.empty(total, dtype=torch.float32).pin_memory()
+        h_out = h_out_pinned.numpy()
+    except RuntimeError:
+        pass
+    spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(max(2, min(args.steps, 5))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * n / statistics.median(e2e_t)
+    h2d = n * 56
+    d2h = total * 4 + n * 24
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels_per_gpu": n, "n_bins": 2000, "tol_l1": TOL,
+                   "path": "plain batched (uniform start), matrix-free dense power step",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}, pixels sharded, no collective"},
+        "iters": {"mean": float(reps["iters"].mean()), "max": int(reps["iters"].max())},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "batch_fused_kernel", "kernel_ms": kms,
+                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock)"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+    }
+    if clocks.get("sm_mhz"):
+        line["roofline"]["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, _ = cpu_sample(px, args.cpu_sample)
+        rate, dt, used = oracle_rate(sample, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": f"{len(sample)} of the 65536 pixels (seed 55), {dt:.1f} s"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--ref-sample", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

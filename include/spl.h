@@ -1,0 +1,190 @@
+/*
+ * libspl — GB300 (sm_103a) engine for the stationary timestamp pmf of an
+ * asynchronous single-photon LiDAR pixel under SPAD dead time
+ * (Zhang, Weerasooriya, Chennuri, Chan, "Real-Time Markov Modeling for
+ * Single-Photon LiDAR", arXiv 2509.20500).
+ *
+ * Problem (Sec. 2.2): given theta = (t_r, t_d, sigma, tau, S, B, n_b), return
+ * the registration pmf f_r over the n_b TCSPC bins, computed as the stationary
+ * distribution pi of the timestamp Markov chain, pi P~ = pi (Sec. 2.3).
+ *
+ * Conventions shared by every call:
+ *  - Times (t_r, t_d, tau, sigma) are in one unit of the caller's choice.
+ *  - Bins are 0-based, bin j covers ((j) Delta, (j+1) Delta] with centre
+ *    s_j = (j + 1/2) Delta, Delta = t_r / n_bins (state set, Sec. 2.3; the
+ *    discretiser D of Sec. 3.1).  The bin width is never passed: the dead-time
+ *    shift is computed from n_bins and t_r as
+ *        q = fmod(t_d, t_r) * n_bins / t_r   (IEEE FP64, in that order)
+ *        l = ceil(q)                         (Theorem 2)
+ *    so dead times on the bin grid give exact integer shifts.
+ *  - Lambda is the flux of one laser period of the Eq. 1 flux, F(t_r): the
+ *    Gaussian pulse is truncated to [0, t_r) and not renormalised.
+ *  - Device pointers are CUDA device addresses owned by the caller (PyTorch
+ *    allocates them); host pointers are ordinary host memory.  "stream" is a
+ *    cudaStream_t passed as void*; NULL means the legacy default stream.
+ *  - Every call returns an spl_status_t and never aborts the process.  On
+ *    SPL_ECUDA the CUDA error is kept for spl_last_cuda_error().
+ *  - Results are FP32 pmfs (sum 1).  Matrix entries and power iterations run
+ *    in FP32; the cumulative flux F, Lambda and the exponentials that turn them
+ *    into per-bin factors run in FP64 on the GPU.
+ */
+#ifndef SPL_H
+#define SPL_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPL_API __attribute__((visibility("default")))
+#else
+#define SPL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One pixel.  n_bins >= 2.  shift_override = -1 uses the paper's row shift
+ * l = ceil(q) (Theorem 2); a value >= 0 forces that shift (for example
+ * ceil(q + 1/2) - 1, which reproduces the sequential shift-then-quantise
+ * construction of Eq. 4 exactly).  Valid input: t_r > 0, sigma > 0, t_d >= 0,
+ * S >= 0, B >= 0, S + B > 0, 0 <= tau < t_r, all finite, Lambda <= 120. */
+typedef struct {
+    double t_r, t_d, tau, sigma, S, B;
+    int32_t n_bins;
+    int32_t shift_override;
+} spl_pixel_t;
+
+typedef enum {
+    SPL_OK = 0,
+    SPL_EINVAL = 1,    /* invalid argument: bad theta, NULL pointer, n < 0, size limit */
+    SPL_ENOMEM = 2,    /* device or host allocation failed */
+    SPL_ECUDA = 3,     /* a CUDA runtime/driver call failed */
+    SPL_ENOCONV = 4,   /* max_iter steps did not meet the stop rule; result is the last iterate */
+    SPL_ETIMEOUT = 5,  /* a bounded device-side wait gave up; result undefined */
+} spl_status_t;
+
+typedef enum {
+    SPL_MATERIALIZED = 0,  /* P stored in HBM (FP32, 4 N^2 bytes); power step is a TMA-staged GEMV */
+    SPL_FUSED = 1,         /* P never stored; power step regenerates each tile of P~ in registers */
+} spl_mode_t;
+
+/* Per-pixel outcome of an iteration. */
+typedef struct {
+    int32_t iters;          /* power steps taken */
+    int32_t status;         /* spl_status_t of this pixel */
+    float last_step_l1;     /* ||pi_k - pi_{k-1}||_1 of the last step */
+    float err_bound;        /* estimated L1 distance of the result to the exact pi */
+    float lambda2_abs;      /* estimate of |lambda_2| of P~ (Sec. 4.1); -1 if none */
+    float lambda2_phase;    /* estimate of arg(lambda_2) in radians, [0, pi] (Sec. 4.2) */
+} spl_report_t;
+
+typedef struct spl_chain spl_chain_t;   /* opaque; owned by the library */
+
+/*
+ * Build the chain of one pixel (Sec. 3.2-3.4).
+ *   Computes, on `stream`, the per-bin flux lambda(s_j) (Eq. 1), the
+ *   cumulative flux F(s_j) and Lambda = F(t_r) (Theorem 1) in FP64, and from
+ *   them the factors of Eq. 6.  mode SPL_MATERIALIZED additionally writes the
+ *   N x N matrix P_ij = lambda(s_j) exp(F(s_p) - F(s_j) - Lambda 1{p > j}),
+ *   p = (i + l) mod N (Eq. 6 after the row roll E = J_l E_base, Sec. 3.4),
+ *   with the roll folded into the row address, plus its row sums.
+ *   *out receives a chain that owns all device scratch it needs; release it
+ *   with spl_free.  The call is asynchronous on `stream` except for its
+ *   device allocations.
+ * Errors: SPL_EINVAL (theta, p == NULL, out == NULL), SPL_ENOMEM, SPL_ECUDA.
+ */
+SPL_API spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *stream, spl_chain_t **out);
+
+/*
+ * Stationary pmf of a built chain by power iteration, pi <- pi P~ with
+ * renormalisation (Sec. 2.3, Sec. 3.4).
+ *   tol      : target L1 error of the result (for example 1e-6).  The stop
+ *              rule bounds the remaining error with the last steps and the
+ *              estimate of lambda_2 (modulus and phase, Sec. 4).
+ *   max_iter : step limit (> 0).
+ *   d_warm   : NULL for the uniform start, else a device vector of n_bins
+ *              nonnegative weights with positive sum (normalised here).
+ *   d_pi     : device output, n_bins floats.
+ *   rep      : host pointer (may be NULL) for the report.
+ * Synchronises the chain's stream (it reads convergence flags back).
+ * Errors: SPL_EINVAL, SPL_ECUDA, SPL_ENOCONV (d_pi holds the last iterate).
+ */
+SPL_API spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_iter, const float *d_warm,
+                            float *d_pi, spl_report_t *rep);
+
+/*
+ * Stationary pmfs of many independent pixels with uneven n_bins in one
+ * persistent launch (matrix-free; one thread block per pixel at a time,
+ * largest pixels first).
+ *   h_pixels  : host array of n pixels.
+ *   tol, max_iter : as in spl_stationary, per pixel.
+ *   d_warm    : NULL or a device array packed like d_out (nonnegative weights).
+ *   d_out     : device output, packed: pixel k occupies
+ *               d_out[d_offsets[k] .. d_offsets[k] + n_bins_k).
+ *   d_offsets : device int64 array [n + 1] of those offsets (caller-owned).
+ *   h_reports : host array [n] or NULL.  When non-NULL the call synchronises
+ *               `stream` to fill it; when NULL the call is asynchronous.
+ * Returns the worst per-pixel status (SPL_ENOCONV < SPL_ETIMEOUT), or
+ * SPL_EINVAL for any invalid pixel (nothing is launched then).
+ */
+SPL_API spl_status_t spl_batch_stationary(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                  const float *d_warm, float *d_out, const int64_t *d_offsets,
+                                  spl_report_t *h_reports, void *stream);
+
+/* Options for spl_batch_stationary_ex. */
+typedef struct {
+    int32_t warm_is_logits;   /* 1: d_warm holds logits, the start is their softmax per pixel */
+    int32_t min_iter;         /* steps always taken before the stop rule may fire (>= 1) */
+    int32_t threads;          /* threads per block, 0 = library default */
+    int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
+} spl_batch_opts_t;
+
+/* spl_batch_stationary with options (opts may be NULL for the defaults). */
+SPL_API spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                     const float *d_warm, float *d_out, const int64_t *d_offsets,
+                                     spl_report_t *h_reports, void *stream, const spl_batch_opts_t *opts);
+
+/* Device time in ms of the batch kernel of the last spl_batch_stationary_ex
+ * call on the current device that set time_kernel (events recorded on that
+ * call's stream just before and after the kernel launch).  Waits for the end
+ * event.  SPL_EINVAL if no timed call was made. */
+SPL_API spl_status_t spl_batch_kernel_ms(float *ms);
+
+/*
+ * Same computation as spl_batch_stationary with HOST buffers: h_warm (NULL or
+ * packed host floats), h_out (packed host floats, offsets from the n_bins of
+ * h_pixels in order) and h_reports (may be NULL).  Copies inputs to the device
+ * and results back inside the call; synchronises `stream`.
+ */
+SPL_API spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                       const float *h_warm, float *h_out, spl_report_t *h_reports,
+                                       void *stream);
+
+/* Materialised chains only: copy P (the paper's unnormalised P of Eq. 4/6,
+ * lambda_j E_ij without the constant 1/(1 - e^-Lambda)) to d_P, row-major
+ * [n_bins][n_bins].  SPL_EINVAL for fused chains. */
+SPL_API spl_status_t spl_matrix(spl_chain_t *c, float *d_P);
+
+/* Per-bin vectors of a built chain, for inspection: d_lambda (FP32 lambda(s_j)),
+ * d_F (FP64 F(s_j)); either may be NULL.  h_Lambda (host, may be NULL) gets
+ * Lambda; h_shift (may be NULL) the row shift in use. */
+SPL_API spl_status_t spl_chain_flux(spl_chain_t *c, float *d_lambda, double *d_F, double *h_Lambda,
+                            int32_t *h_shift);
+
+/* Release a chain (NULL is ignored). */
+SPL_API void spl_free(spl_chain_t *c);
+
+/* Static text for a status. */
+SPL_API const char *spl_strerror(spl_status_t s);
+
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+SPL_API const char *spl_last_cuda_error(void);
+
+/* Library version string. */
+SPL_API const char *spl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPL_H */

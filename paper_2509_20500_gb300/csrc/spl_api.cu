@@ -1,0 +1,642 @@
+// libspl C ABI (declared in include/spl.h): validation, the dead-time shift
+// (Theorem 2), chain objects, the iteration driver and the batch driver.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "spl.h"
+#include "spl_kernels.h"
+
+using namespace spl;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+spl_status_t cuda_fail(cudaError_t e, const char *where) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+    return SPL_ECUDA;
+}
+
+#define SPL_CU(expr)                                                   \
+    do {                                                               \
+        cudaError_t e_ = (expr);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);            \
+    } while (0)
+
+bool finite_all(const spl_pixel_t &p) {
+    return std::isfinite(p.t_r) && std::isfinite(p.t_d) && std::isfinite(p.tau) && std::isfinite(p.sigma) &&
+           std::isfinite(p.S) && std::isfinite(p.B);
+}
+
+// Largest Lambda accepted: exp(+-Lambda/2) must stay inside FP32 with room for
+// N-term sums (see the factorisation in spl_device.cuh).
+constexpr double kLambdaMax = 120.0;
+constexpr int32_t kMaxBins = 1 << 24;
+
+// a1: validate and derive the row shift.  q = fmod(t_d, t_r) * N / t_r is
+// evaluated in IEEE FP64 in that order (no contraction: a product then a
+// quotient), l = ceil(q) (Theorem 2), reduced modulo N.
+spl_status_t make_pixel(const spl_pixel_t &p, PixelDev &d) {
+    if (!finite_all(p)) return SPL_EINVAL;
+    if (p.n_bins < 2 || p.n_bins > kMaxBins) return SPL_EINVAL;
+    if (!(p.t_r > 0.0) || !(p.sigma > 0.0) || p.t_d < 0.0 || p.S < 0.0 || p.B < 0.0) return SPL_EINVAL;
+    if (!(p.S + p.B > 0.0)) return SPL_EINVAL;
+    if (p.tau < 0.0 || p.tau >= p.t_r) return SPL_EINVAL;
+    if (p.S + p.B > kLambdaMax) return SPL_EINVAL;
+    if (p.shift_override < -1) return SPL_EINVAL;
+    const int32_t N = p.n_bins;
+    int64_t l;
+    if (p.shift_override >= 0) {
+        l = p.shift_override;
+    } else {
+        const volatile double x_d = std::fmod(p.t_d, p.t_r);
+        const volatile double num = x_d * (double)N;
+        const double q = num / p.t_r;
+        l = (int64_t)std::ceil(q);
+    }
+    l %= N;
+    if (l < 0) l += N;
+    d.t_r = p.t_r;
+    d.tau = p.tau;
+    d.sigma = p.sigma;
+    d.S = p.S;
+    d.B = p.B;
+    d.N = N;
+    d.l = (int32_t)l;
+    d.out_off = 0;
+    d.index = 0;
+    d.pad_ = 0;
+    return SPL_OK;
+}
+
+int num_sms_current() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return sms > 0 ? sms : 1;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+}  // namespace
+
+// ======================================================================
+// Chains
+// ======================================================================
+
+struct spl_chain {
+    PixelDev p{};
+    spl_mode_t mode = SPL_FUSED;
+    cudaStream_t stream = nullptr;
+    int N = 0, vlen = 0, ld = 0;
+    // per-bin vectors
+    float *w = nullptr, *u = nullptr, *lam = nullptr;
+    double *F = nullptr, *scal = nullptr;
+    float *rowsum = nullptr, *rho = nullptr;
+    // iteration vectors
+    float *pi = nullptr, *y = nullptr, *d1 = nullptr, *d2 = nullptr, *v = nullptr;
+    float *part = nullptr;
+    ChainState *state = nullptr;
+    ChainState *h_state = nullptr;   // pinned readback
+    int *err_flag = nullptr;
+    // materialised
+    float *P = nullptr;
+    CUtensorMap tmap{};
+    int gemv_grid = 0, tiles_per_slab = 0, tiles_per_cta = 0, total_tiles = 0;
+    // fused split
+    int chunks = 0, chunk = 0, ld_part = 0;
+};
+
+static void chain_release(spl_chain *c) {
+    if (!c) return;
+    void *bufs[] = {c->w, c->u, c->lam, c->F, c->scal, c->rowsum, c->rho, c->pi, c->y,
+                    c->d1, c->d2, c->v, c->part, c->state, c->err_flag, c->P};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    delete c;
+}
+
+static spl_status_t chain_alloc(spl_chain *c) {
+    const int N = c->N, vl = c->vlen;
+    SPL_CU(dalloc(&c->w, vl));
+    SPL_CU(dalloc(&c->u, vl));
+    SPL_CU(dalloc(&c->lam, N));
+    SPL_CU(dalloc(&c->F, N));
+    SPL_CU(dalloc(&c->scal, 2));
+    SPL_CU(dalloc(&c->rowsum, N));
+    SPL_CU(dalloc(&c->rho, vl));
+    SPL_CU(dalloc(&c->pi, N));
+    SPL_CU(dalloc(&c->y, N));
+    SPL_CU(dalloc(&c->d1, N));
+    SPL_CU(dalloc(&c->d2, N));
+    SPL_CU(dalloc(&c->v, vl));
+    SPL_CU(dalloc(&c->state, 1));
+    SPL_CU(dalloc(&c->err_flag, 1));
+    SPL_CU(cudaMallocHost(reinterpret_cast<void **>(&c->h_state), sizeof(ChainState)));
+    return SPL_OK;
+}
+
+// Split layout for the multi-CTA dense passes: enough CTAs to cover every SM
+// a few times with whole 128-entry chunks of the broadcast vector.
+static void plan_split(spl_chain *c) {
+    const int sms = num_sms_current();
+    const int col_tiles = (c->N + split_cols_per_cta() - 1) / split_cols_per_cta();
+    const int nblk = c->vlen / 128;
+    int chunks = (4 * sms + col_tiles - 1) / col_tiles;
+    chunks = std::max(1, std::min(chunks, nblk));
+    const int blk_per_chunk = (nblk + chunks - 1) / chunks;
+    c->chunk = blk_per_chunk * 128;
+    c->chunks = (c->vlen + c->chunk - 1) / c->chunk;
+    c->ld_part = c->vlen;
+}
+
+extern "C" spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *stream, spl_chain_t **out) {
+    if (!p || !out) return SPL_EINVAL;
+    *out = nullptr;
+    if (mode != SPL_MATERIALIZED && mode != SPL_FUSED) return SPL_EINVAL;
+    PixelDev d;
+    spl_status_t st = make_pixel(*p, d);
+    if (st != SPL_OK) return st;
+    spl_chain *c = new (std::nothrow) spl_chain();
+    if (!c) return SPL_ENOMEM;
+    c->p = d;
+    c->mode = mode;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->N = d.N;
+    c->vlen = split_pad_len(d.N);
+    plan_split(c);
+    st = chain_alloc(c);
+    if (st != SPL_OK) { chain_release(c); return st; }
+    cudaStream_t s = c->stream;
+    cudaError_t e = launch_chain_flux(d, c->w, c->u, c->lam, c->F, c->scal, c->vlen, s);
+    if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "chain_flux"); }
+    if (mode == SPL_MATERIALIZED) {
+        const int N = d.N;
+        c->ld = (N + 31) / 32 * 32;
+        e = dalloc(&c->P, (size_t)N * c->ld);
+        if (e != cudaSuccess) { chain_release(c); return e == cudaErrorMemoryAllocation ? SPL_ENOMEM : cuda_fail(e, "P"); }
+        e = launch_build_matrix(N, d.l, c->ld, c->w, c->u, c->scal, c->P, c->rowsum, num_sms_current(), s);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "build_matrix"); }
+        // TMA descriptor over P: dims {cols, rows}, row pitch ld floats, 128 x 32 boxes.
+        auto enc = get_encode_tiled();
+        if (!enc) { chain_release(c); return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
+        cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
+        cuuint64_t gstride[1] = {(cuuint64_t)c->ld * sizeof(float)};
+        cuuint32_t box[2] = {128, 32};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->P, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) { chain_release(c); return cuda_fail(cudaErrorInvalidValue, "tensor map encode"); }
+        const int slabs = (N + 127) / 128;
+        c->tiles_per_slab = (N + 31) / 32;
+        c->total_tiles = slabs * c->tiles_per_slab;
+        int grid = num_sms_current();
+        if (grid < slabs) grid = slabs;
+        c->tiles_per_cta = (c->total_tiles + grid - 1) / grid;
+        if (c->tiles_per_cta > c->tiles_per_slab) c->tiles_per_cta = c->tiles_per_slab;
+        c->gemv_grid = (c->total_tiles + c->tiles_per_cta - 1) / c->tiles_per_cta;
+        e = dalloc(&c->part, (size_t)c->gemv_grid * 2 * 128);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "part"); }
+        e = cudaMemsetAsync(c->part, 0, sizeof(float) * (size_t)c->gemv_grid * 2 * 128, s);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "memset part"); }
+    } else {
+        e = dalloc(&c->part, (size_t)c->chunks * c->ld_part);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "part"); }
+        // row pass: v = w, per-output factor u
+        TriSplitArgs ta{};
+        ta.N = d.N;
+        ta.vlen = c->vlen;
+        ta.chunk = c->chunk;
+        ta.v = c->w;
+        ta.m = c->u;
+        ta.scal = c->scal;
+        ta.part = c->part;
+        ta.ld_part = c->ld_part;
+        ta.state = nullptr;
+        e = launch_tri_split(ta, true, c->chunks, s);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "row pass"); }
+        e = launch_finish_rows(d.N, c->chunks, c->ld_part, c->part, c->u, c->rho, c->rowsum, d.l, s);
+        if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "finish rows"); }
+    }
+    *out = c;
+    return SPL_OK;
+}
+
+static FinishArgs finish_args(spl_chain *c) {
+    FinishArgs a{};
+    a.mode = c->mode == SPL_MATERIALIZED ? 0 : 1;
+    a.N = c->N;
+    a.l = c->p.l;
+    a.vlen = c->vlen;
+    a.tiles_per_slab = c->tiles_per_slab;
+    a.tiles_per_cta = c->tiles_per_cta;
+    a.nparts = c->chunks;
+    a.ld_part = c->ld_part;
+    a.part = c->part;
+    a.y = c->y;
+    a.pi = c->pi;
+    a.d1 = c->d1;
+    a.d2 = c->d2;
+    a.rowsum = c->rowsum;
+    a.rho = c->rho;
+    a.v = c->v;
+    a.state = c->state;
+    return a;
+}
+
+// One power step: the dense pass (GEMV over P, or the regenerated split
+// column pass) followed by the finish kernel.
+static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa) {
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    if (c->mode == SPL_MATERIALIZED) {
+        GemvArgs g{};
+        g.N = c->N;
+        g.tiles_per_slab = c->tiles_per_slab;
+        g.total_tiles = c->total_tiles;
+        g.tiles_per_cta = c->tiles_per_cta;
+        g.c = c->v;
+        g.part = c->part;
+        g.state = c->state;
+        g.err_flag = c->err_flag;
+        e = launch_gemv(&c->tmap, g, c->gemv_grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "gemv");
+    } else {
+        TriSplitArgs ta{};
+        ta.N = c->N;
+        ta.vlen = c->vlen;
+        ta.chunk = c->chunk;
+        ta.v = c->v;
+        ta.m = c->w;
+        ta.scal = c->scal;
+        ta.part = c->part;
+        ta.ld_part = c->ld_part;
+        ta.state = c->state;
+        e = launch_tri_split(ta, false, c->chunks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "column pass");
+    }
+    e = launch_finish_step(fa, s);
+    if (e != cudaSuccess) return cuda_fail(e, "finish step");
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_iter, const float *d_warm,
+                                       float *d_pi, spl_report_t *rep) {
+    if (!c || !d_pi || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
+    cudaStream_t s = c->stream;
+    ChainState init{};
+    init.tol_err = (float)(0.5 * tol);
+    init.max_iter = max_iter;
+    init.min_iter = 1;
+    init.done = 0;
+    SPL_CU(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    SPL_CU(cudaMemcpyAsync(c->state, &init, sizeof(ChainState), cudaMemcpyHostToDevice, s));
+    const FinishArgs fa = finish_args(c);
+    SPL_CU(launch_init_iter(fa, d_warm, s));
+    // Steps are issued in chunks; every kernel exits at once when the device
+    // state says done, so over-issuing within a chunk costs only launches.
+    int issued = 0;
+    const int chunk = 4;
+    for (;;) {
+        const int n = std::min(chunk, max_iter - issued);
+        for (int i = 0; i < n; ++i) {
+            spl_status_t st = chain_step(c, fa);
+            if (st != SPL_OK) return st;
+        }
+        issued += n;
+        SPL_CU(cudaMemcpyAsync(c->h_state, c->state, sizeof(ChainState), cudaMemcpyDeviceToHost, s));
+        SPL_CU(cudaStreamSynchronize(s));
+        if (c->h_state->done || issued >= max_iter) break;
+    }
+    int herr = 0;
+    SPL_CU(cudaMemcpyAsync(&herr, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPL_CU(cudaMemcpyAsync(d_pi, c->pi, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, s));
+    SPL_CU(cudaStreamSynchronize(s));
+    const ChainState &h = *c->h_state;
+    spl_status_t st = herr ? SPL_ETIMEOUT : (h.done && h.status == ST_OK ? SPL_OK : SPL_ENOCONV);
+    if (rep) {
+        rep->iters = h.st.k;
+        rep->status = st;
+        rep->last_step_l1 = h.st.k > 0 ? h.st.delta[(h.st.k - 1) & 7] : 0.f;
+        rep->err_bound = h.st.err;
+        rep->lambda2_abs = h.st.rho;
+        rep->lambda2_phase = h.st.theta;
+    }
+    return st;
+}
+
+extern "C" spl_status_t spl_matrix(spl_chain_t *c, float *d_P) {
+    if (!c || !d_P || c->mode != SPL_MATERIALIZED) return SPL_EINVAL;
+    SPL_CU(cudaMemcpy2DAsync(d_P, sizeof(float) * c->N, c->P, sizeof(float) * c->ld, sizeof(float) * c->N, c->N,
+                             cudaMemcpyDeviceToDevice, c->stream));
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_chain_flux(spl_chain_t *c, float *d_lambda, double *d_F, double *h_Lambda,
+                                       int32_t *h_shift) {
+    if (!c) return SPL_EINVAL;
+    if (d_lambda)
+        SPL_CU(cudaMemcpyAsync(d_lambda, c->lam, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_F) SPL_CU(cudaMemcpyAsync(d_F, c->F, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    if (h_Lambda) {
+        SPL_CU(cudaMemcpyAsync(h_Lambda, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SPL_CU(cudaStreamSynchronize(c->stream));
+    }
+    if (h_shift) *h_shift = c->p.l;
+    return SPL_OK;
+}
+
+extern "C" void spl_free(spl_chain_t *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    chain_release(c);
+}
+
+// ======================================================================
+// Batch
+// ======================================================================
+
+namespace {
+
+// Device workspace reused across batch calls (grown on demand), one per
+// device.  Calls on one device are serialised by its mutex.
+struct BatchWorkspace {
+    std::mutex mu;
+    PixelDev *px = nullptr;
+    size_t px_cap = 0;
+    ReportDev *reps = nullptr;
+    size_t reps_cap = 0;
+    float *scratch = nullptr;
+    size_t scratch_cap = 0;
+    int *counter = nullptr;
+    size_t counter_cap = 0;
+    // staging of the host-buffer entry point
+    float *d_warm = nullptr, *d_out = nullptr;
+    size_t warm_cap = 0, out_cap = 0;
+    int64_t *d_off = nullptr;
+    size_t off_cap = 0;
+    PixelDev *h_px = nullptr;        // pinned
+    size_t h_px_cap = 0;
+    ReportDev *h_reps = nullptr;     // pinned
+    size_t h_reps_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+};
+
+constexpr int kMaxDevices = 64;
+BatchWorkspace g_ws[kMaxDevices];
+
+template <typename T>
+cudaError_t grow(T **p, size_t *cap, size_t need) {
+    if (*cap >= need && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = std::max(need, (size_t)1);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+template <typename T>
+cudaError_t grow_host(T **p, size_t *cap, size_t need) {
+    if (*cap >= need && *p) return cudaSuccess;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = std::max(need, (size_t)1);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(p), sizeof(T) * n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+spl_status_t ws_get(BatchWorkspace **out) {
+    int dev = 0;
+    SPL_CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return SPL_EINVAL;
+    *out = &g_ws[dev];
+    return SPL_OK;
+}
+
+spl_status_t status_of_alloc(cudaError_t e, const char *what) {
+    return e == cudaErrorMemoryAllocation ? SPL_ENOMEM : cuda_fail(e, what);
+}
+
+// Validates the pixels and writes the work list (sorted by decreasing N,
+// ties by caller order) into pinned staging.  Offsets follow the caller's
+// packed layout: either h_offsets (host) or the running sum of n_bins.
+spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int32_t n, int *nmax_out) {
+    cudaError_t e = grow_host(&ws.h_px, &ws.h_px_cap, (size_t)n);
+    if (e != cudaSuccess) return status_of_alloc(e, "pinned work list");
+    std::vector<int32_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return h_pixels[a].n_bins > h_pixels[b].n_bins; });
+    std::vector<int64_t> off((size_t)n + 1, 0);
+    for (int32_t k = 0; k < n; ++k) off[k + 1] = off[k] + h_pixels[k].n_bins;
+    int nmax = 2;
+    for (int32_t r = 0; r < n; ++r) {
+        const int32_t k = order[r];
+        PixelDev d;
+        spl_status_t st = make_pixel(h_pixels[k], d);
+        if (st != SPL_OK) return st;
+        d.out_off = off[k];
+        d.index = k;
+        ws.h_px[r] = d;
+        nmax = std::max(nmax, (int)d.N);
+    }
+    *nmax_out = nmax;
+    return SPL_OK;
+}
+
+// Launches the persistent batch kernel; out/warm are packed by caller order.
+spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
+                       int warm_logits, int min_iter, int threads_req, float *d_out, const int64_t *d_offsets,
+                       cudaStream_t s, bool time_kernel = false) {
+    const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
+    if (threads != 256 && threads != 512 && threads != 1024) return SPL_EINVAL;
+    const int npad = batch_pad_len(nmax);
+    const size_t smem = (size_t)3 * npad * sizeof(float);
+    if (smem > 227 * 1024) return SPL_EINVAL;
+    int bps = 0;
+    SPL_CU(batch_occupancy(threads, smem, &bps));
+    if (bps < 1) return SPL_EINVAL;
+    int grid = bps * num_sms_current();
+    if (grid > n) grid = n;
+    cudaError_t e;
+    if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
+    if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
+    if ((e = grow(&ws.counter, &ws.counter_cap, 1)) != cudaSuccess) return status_of_alloc(e, "counter");
+    if ((e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * 5 * npad)) != cudaSuccess)
+        return status_of_alloc(e, "scratch");
+    SPL_CU(cudaMemcpyAsync(ws.px, ws.h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
+    SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
+    BatchArgs a{};
+    a.px = ws.px;
+    a.n = n;
+    a.counter = ws.counter;
+    a.warm = d_warm;
+    a.warm_logits = warm_logits;
+    a.out = d_out;
+    a.offsets = d_offsets;
+    a.reports = ws.reps;
+    a.scratch = ws.scratch;
+    a.npad_max = npad;
+    a.tol_err = (float)(0.5 * tol);
+    a.max_iter = max_iter;
+    a.min_iter = std::max(1, min_iter);
+    if (time_kernel) {
+        if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
+        if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
+        SPL_CU(cudaEventRecord(ws.ev0, s));
+    }
+    SPL_CU(launch_batch(a, threads, grid, smem, s));
+    if (time_kernel) {
+        SPL_CU(cudaEventRecord(ws.ev1, s));
+        ws.timed = true;
+    }
+    return SPL_OK;
+}
+
+spl_status_t collect_reports(BatchWorkspace &ws, int32_t n, spl_report_t *h_reports, cudaStream_t s) {
+    cudaError_t e = grow_host(&ws.h_reps, &ws.h_reps_cap, (size_t)n);
+    if (e != cudaSuccess) return status_of_alloc(e, "pinned reports");
+    SPL_CU(cudaMemcpyAsync(ws.h_reps, ws.reps, sizeof(ReportDev) * n, cudaMemcpyDeviceToHost, s));
+    SPL_CU(cudaStreamSynchronize(s));
+    spl_status_t worst = SPL_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        const ReportDev &r = ws.h_reps[k];
+        spl_report_t &o = h_reports[k];
+        o.iters = r.iters;
+        o.status = r.status;
+        o.last_step_l1 = r.last_step_l1;
+        o.err_bound = r.err_bound;
+        o.lambda2_abs = r.lambda2_abs;
+        o.lambda2_phase = r.lambda2_phase;
+        if (r.status > (int)worst) worst = (spl_status_t)r.status;
+    }
+    return worst;
+}
+
+}  // namespace
+
+extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                                const float *d_warm, float *d_out, const int64_t *d_offsets,
+                                                spl_report_t *h_reports, void *stream, const spl_batch_opts_t *opts) {
+    if (n < 0 || (n > 0 && (!h_pixels || !d_out || !d_offsets)) || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
+    if (n == 0) return SPL_OK;
+    BatchWorkspace *ws = nullptr;
+    spl_status_t st = ws_get(&ws);
+    if (st != SPL_OK) return st;
+    std::lock_guard<std::mutex> lock(ws->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int nmax = 0;
+    st = make_work_list(*ws, h_pixels, n, &nmax);
+    if (st != SPL_OK) return st;
+    const int logits = opts ? opts->warm_is_logits : 0;
+    const int min_iter = opts ? opts->min_iter : 1;
+    const int threads = opts ? opts->threads : 0;
+    const bool timed = opts && opts->time_kernel;
+    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, logits, min_iter, threads, d_out, d_offsets, s, timed);
+    if (st != SPL_OK) return st;
+    if (h_reports) return collect_reports(*ws, n, h_reports, s);
+    // The pinned work list is read by the copy engine asynchronously; keep the
+    // next call from overwriting it before that copy ran.
+    SPL_CU(cudaStreamSynchronize(s));
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_batch_stationary(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                             const float *d_warm, float *d_out, const int64_t *d_offsets,
+                                             spl_report_t *h_reports, void *stream) {
+    return spl_batch_stationary_ex(h_pixels, n, tol, max_iter, d_warm, d_out, d_offsets, h_reports, stream, nullptr);
+}
+
+extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol,
+                                                  int32_t max_iter, const float *h_warm, float *h_out,
+                                                  spl_report_t *h_reports, void *stream) {
+    if (n < 0 || (n > 0 && (!h_pixels || !h_out)) || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
+    if (n == 0) return SPL_OK;
+    BatchWorkspace *ws = nullptr;
+    spl_status_t st = ws_get(&ws);
+    if (st != SPL_OK) return st;
+    std::lock_guard<std::mutex> lock(ws->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int nmax = 0;
+    st = make_work_list(*ws, h_pixels, n, &nmax);
+    if (st != SPL_OK) return st;
+    size_t total = 0;
+    for (int32_t k = 0; k < n; ++k) total += (size_t)h_pixels[k].n_bins;
+    cudaError_t e;
+    if ((e = grow(&ws->d_out, &ws->out_cap, total)) != cudaSuccess) return status_of_alloc(e, "out");
+    if (h_warm) {
+        if ((e = grow(&ws->d_warm, &ws->warm_cap, total)) != cudaSuccess) return status_of_alloc(e, "warm");
+        SPL_CU(cudaMemcpyAsync(ws->d_warm, h_warm, sizeof(float) * total, cudaMemcpyHostToDevice, s));
+    }
+    st = run_batch(*ws, n, nmax, tol, max_iter, h_warm ? ws->d_warm : nullptr, 0, 1, 0, ws->d_out, nullptr, s);
+    if (st != SPL_OK) return st;
+    SPL_CU(cudaMemcpyAsync(h_out, ws->d_out, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    if (h_reports) return collect_reports(*ws, n, h_reports, s);
+    SPL_CU(cudaStreamSynchronize(s));
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_batch_kernel_ms(float *ms) {
+    if (!ms) return SPL_EINVAL;
+    BatchWorkspace *ws = nullptr;
+    spl_status_t st = ws_get(&ws);
+    if (st != SPL_OK) return st;
+    std::lock_guard<std::mutex> lock(ws->mu);
+    if (!ws->timed) return SPL_EINVAL;
+    SPL_CU(cudaEventSynchronize(ws->ev1));
+    SPL_CU(cudaEventElapsedTime(ms, ws->ev0, ws->ev1));
+    return SPL_OK;
+}
+
+// ======================================================================
+// Misc
+// ======================================================================
+
+extern "C" const char *spl_strerror(spl_status_t s) {
+    switch (s) {
+        case SPL_OK: return "ok";
+        case SPL_EINVAL: return "invalid argument";
+        case SPL_ENOMEM: return "out of memory";
+        case SPL_ECUDA: return "CUDA error";
+        case SPL_ENOCONV: return "power iteration did not converge within max_iter";
+        case SPL_ETIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *spl_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" const char *spl_version(void) { return "libspl 0.1 (sm_103a)"; }

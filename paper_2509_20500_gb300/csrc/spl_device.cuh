@@ -1,0 +1,293 @@
+// Device-side building blocks shared by the libspl kernels (sm_103a).
+//
+// Notation (0-based): N bins, Delta = t_r / N, s_j = (j + 1/2) Delta,
+// l = row shift, p_i = (i + l) mod N, Lambda = F(t_r), eL = exp(-Lambda).
+//
+// Eq. 6 with the roll of Sec. 3.4 gives the unnormalised kernel
+//     P_ij = lambda_j exp(F_p - F_j - Lambda 1{p > j}),   p = p_i.
+// It factors exactly into a row factor, a column factor and a two-valued
+// triangle weight:
+//     P_ij = u_p * w_j * mu(p, j),   u_k = exp(F_k - Lambda/2),
+//     w_j = lambda_j exp(Lambda/2 - F_j),   mu(k, j) = 1 if k <= j else eL.
+// (The Lambda/2 centring keeps both factors inside FP32 range for Lambda up
+// to 120; it cancels in the product.)  u and w are formed in FP64 from the
+// FP64 cumulative flux and rounded once to FP32, so a matrix entry carries
+// ~2 FP32 roundings instead of the ~1e-6 relative error an FP32 exponent of
+// a difference of cumulative fluxes of size ~10 would carry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spl {
+
+// Per-pixel parameters after host validation.  t_d is already folded into l.
+struct PixelDev {
+    double t_r, tau, sigma, S, B;
+    int32_t N;
+    int32_t l;            // row shift in [0, N)
+    int64_t out_off;      // offset of this pixel's pmf in the packed output
+    int32_t index;        // position of the pixel in the caller's array
+    int32_t pad_;
+};
+
+// Per-pixel result record written by the kernels (mirrors spl_report_t).
+struct ReportDev {
+    int32_t iters;
+    int32_t status;
+    float last_step_l1;
+    float err_bound;
+    float lambda2_abs;
+    float lambda2_phase;
+};
+
+// Status codes used on the device (same values as spl_status_t).
+enum : int32_t { ST_OK = 0, ST_ENOCONV = 4, ST_ETIMEOUT = 5 };
+
+// ---------------------------------------------------------------- a2: flux, FP64
+
+// Standard normal CDF via erfc (relative accuracy in both tails).
+__device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752440); }
+
+// Beyond |z| = 9 the Gaussian CDF is 0 or 1 to below 1.2e-19 and its density
+// below 1.1e-18, far under FP64 resolution of F (>= B s_j / t_r) and of
+// lambda (>= B / t_r) for every admissible pixel, so the erfc/exp is skipped.
+constexpr double kTailZ = 9.0;
+
+struct FluxConst {
+    double Phi0;          // Phi(-tau / sigma)
+    double Lambda;        // F(t_r), flux of one period (Theorem 1)
+    double gnorm;         // 1 / (sigma sqrt(2 pi))
+    double delta;         // t_r / N
+};
+
+__device__ __forceinline__ FluxConst flux_const(const PixelDev &p) {
+    FluxConst c;
+    c.Phi0 = std_cdf(-p.tau / p.sigma);
+    const double zr = (p.t_r - p.tau) / p.sigma;
+    const double Phir = (zr > kTailZ) ? 1.0 : std_cdf(zr);
+    c.Lambda = p.S * (Phir - c.Phi0) + p.B;
+    c.gnorm = 0.39894228040143267794 / p.sigma;
+    c.delta = p.t_r / (double)p.N;
+    return c;
+}
+
+// Eq. 1 flux lambda(s_j) and Theorem 1's F(s_j) = S [Phi(z_j) - Phi(z_0)] + B s_j / t_r.
+__device__ __forceinline__ void flux_bin(const PixelDev &p, const FluxConst &c, int j,
+                                         double &F, double &lam) {
+    const double s = ((double)j + 0.5) * c.delta;
+    const double z = (s - p.tau) / p.sigma;
+    double G, g;
+    if (fabs(z) <= kTailZ) {
+        G = std_cdf(z) - c.Phi0;
+        g = exp(-0.5 * z * z) * c.gnorm;
+    } else {
+        G = (z > 0.0 ? 1.0 : 0.0) - c.Phi0;
+        g = 0.0;
+    }
+    F = p.S * G + p.B * (s / p.t_r);
+    lam = p.S * g + p.B / p.t_r;
+}
+
+// Column and row factors of bin j (see the header comment).
+__device__ __forceinline__ void factors_bin(const PixelDev &p, const FluxConst &c, int j,
+                                            float &w, float &u) {
+    double F, lam;
+    flux_bin(p, c, j, F, lam);
+    const double e = exp(0.5 * c.Lambda - F);     // exp(Lambda/2 - F_j)
+    w = (float)(lam * e);
+    u = (float)(1.0 / e);
+}
+
+// ---------------------------------------------------------------- block reductions
+
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float *red) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (wid == 0) {
+        t = (lane < NW) ? red[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// Sums K values at once (one pass of barriers); results land in out[0..K).
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_k(float (&v)[K], float *red /* >= K * NT/32 */) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * NW + wid] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float t = (lane < NW) ? red[k * NW + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[K * NW + k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = red[K * NW + k];
+}
+
+// ---------------------------------------------------------------- stop rule
+
+// Convergence state of one pixel's power iteration.  The error of the
+// current iterate pi_k is bounded by the tail sum of the steps,
+//   ||pi_k - pi|| <= sum_{m > k} delta_m,
+// and the steps decay like |lambda_2|^m with an oscillation of frequency
+// arg(lambda_2) (Sec. 4).  |lambda_2| and its phase are estimated from the
+// step vectors d_k = pi_k - pi_{k-1} by fitting d_k = a d_{k-1} + b d_{k-2}
+// (the roots of z^2 = a z + b are the dominant subdominant eigenvalue pair);
+// the decayed envelope of the last W steps, W ~ one oscillation period,
+// times rho / (1 - rho), bounds the remaining error.
+struct StopState {
+    float delta[8];       // last steps (ring, newest at (k-1) & 7)
+    float g11, g12, g22;  // <d_{k-1},d_{k-1}>, <d_{k-1},d_{k-2}>, <d_{k-2},d_{k-2}>
+    float rho, theta;     // current |lambda_2| and phase estimates (rho < 0: none yet)
+    float err;            // last error bound
+    int32_t k;            // steps taken
+    int32_t reliable;     // 1 once a fit was made on steps well above FP32 noise
+};
+
+// Steps above this L1 size are far above the FP32 rounding noise of an
+// iterate (~1e-7), so the recurrence fit on them is trustworthy.
+constexpr float kFitFloor = 3e-6f;
+// Modulus assumed for lambda_2 while no trustworthy fit exists (a start that
+// is already within noise of pi).  Over S, B in [0.01, 10] and t_d in
+// [20, 150] (t_r = 100) the largest |lambda_2| is about 0.87.
+constexpr float kRhoDefault = 0.9f;
+// Below this L1 step the step-to-step ratio is dominated by rounding noise
+// and is not used to raise the modulus estimate.
+constexpr float kRatioFloor = 1e-6f;
+// Below this L1 step a step envelope that has stopped shrinking (the last
+// two steps at least 0.95 of the two before, slower than any |lambda_2| <=
+// 0.97 allows) marks the FP32 rounding floor of the map (about one unit in
+// the last place per element, ~1e-7 in L1): further steps cannot reduce
+// the error.
+constexpr float kStallFloor = 3e-7f;
+
+__host__ __device__ __forceinline__ void stop_init(StopState &s) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s.delta[i] = 0.f;
+    s.g11 = s.g12 = s.g22 = 0.f;
+    s.rho = -1.f;
+    s.theta = 0.f;
+    s.err = INFINITY;
+    s.k = 0;
+    s.reliable = 0;
+}
+
+// Fit of the 2-term recurrence from the Gram data; returns false if degenerate.
+__host__ __device__ __forceinline__ bool fit_lambda2(float g11, float g12, float g22, float h1, float h2,
+                                            float &rho, float &theta) {
+    if (!(g11 > 0.f) || !(g22 > 0.f)) return false;
+    const double G11 = g11, G12 = g12, G22 = g22, H1 = h1, H2 = h2;
+    const double det = G11 * G22 - G12 * G12;
+    double a, b;
+    // Nearly collinear steps (one real mode dominates, or two close real
+    // modes the FP32 Gram data cannot separate): single-mode ratio.
+    if (det <= 1e-3 * G11 * G22) {
+        a = H1 / G11;
+        rho = (float)fabs(a);
+        theta = a >= 0.0 ? 0.f : 3.14159265358979f;
+        return true;
+    }
+    a = (H1 * G22 - H2 * G12) / det;
+    b = (G11 * H2 - G12 * H1) / det;
+    const double disc = a * a + 4.0 * b;
+    if (disc < 0.0) {
+        rho = (float)sqrt(-b);
+        theta = (float)atan2(sqrt(-disc), a);
+    } else {
+        const double sq = sqrt(disc);
+        const double r1 = 0.5 * (a + sq), r2 = 0.5 * (a - sq);
+        const double r = fabs(r1) >= fabs(r2) ? r1 : r2;
+        rho = (float)fabs(r);
+        theta = r >= 0.0 ? 0.f : 3.14159265358979f;
+    }
+    return true;
+}
+
+// Consume one step's reductions: delta = ||d_k||_1, dd = <d_k,d_k>,
+// d1 = <d_k,d_{k-1}>, d2 = <d_k,d_{k-2}>.  Returns true when the bound on the
+// error of pi_k is below tol_err (and k >= min_iter).
+__host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, float dd, float d1, float d2,
+                                            float tol_err, int min_iter) {
+    s.k += 1;
+    const int k = s.k;
+    s.delta[(k - 1) & 7] = delta;
+    if (k >= 3) {
+        const bool trusted = delta > kFitFloor;
+        if (trusted || !s.reliable) {
+            float r, th;
+            if (fit_lambda2(s.g11, s.g12, s.g22, d1, d2, r, th)) {
+                s.rho = r;
+                s.theta = th;
+                s.reliable = trusted ? 1 : 0;
+            }
+        }
+    }
+    // shift the Gram window: new d_{k-1} := d_k, d_{k-2} := d_{k-1}
+    s.g22 = s.g11;
+    s.g12 = d1;
+    s.g11 = dd;
+    if (k < 3) return false;
+    float ru;
+    int W = 2;
+    const float prev = s.delta[(k - 2) & 7];
+    if (s.reliable) {
+        ru = s.rho;
+        if (prev > 0.f && delta > kRatioFloor) {
+            const float ratio = delta / prev;
+            if (ratio < 1.f) ru = fmaxf(ru, ratio);
+        }
+        ru = fminf(fmaxf(ru, 0.05f), 0.9999f);
+        if (s.theta >= 0.2f) W = min(8, max(2, (int)ceilf(6.2831853f / s.theta)));
+    } else {
+        ru = kRhoDefault;
+    }
+    W = min(W, k);
+    float env = 0.f, pw = 1.f;
+    for (int m = 0; m < W; ++m) {
+        env = fmaxf(env, s.delta[(k - 1 - m) & 7] * pw);
+        pw *= ru;
+    }
+    s.err = env * ru / (1.f - ru);
+    if (delta == 0.f) s.err = 0.f;   // exact FP32 fixed point
+    bool stalled = false;
+    if (k >= 4 && delta < kStallFloor) {
+        const float e_now = fmaxf(delta, prev);
+        const float e_old = fmaxf(s.delta[(k - 3) & 7], s.delta[(k - 4) & 7]);
+        stalled = e_now >= 0.95f * e_old;
+    }
+    return k >= min_iter && (s.err < tol_err || stalled);
+}
+
+// ---------------------------------------------------------------- bounded waits
+
+// Spin limit for any device-side wait (mbarrier phases, flags).
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+}  // namespace spl

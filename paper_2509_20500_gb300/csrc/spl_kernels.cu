@@ -1,0 +1,835 @@
+// libspl kernels for sm_103a: cumulative flux (K1), materialised build (K2),
+// TMA-staged GEMV power step (K3), matrix-free power step (K4), the
+// persistent batch driver (K5) and the per-step finish kernel.
+//
+// All power steps compute y_j = sum_i pi_i P~_ij with P~ = row-normalised P
+// (Sec. 2.3).  Using the factorisation of Eq. 6 (see spl_device.cuh),
+//   P~_ij = (u_p / r_i) * w_j * mu(p, j),  p = (i + l) mod N,
+// so in "p-space" (k = p_i, i = (k - l) mod N) the step reads
+//   y_j = sum_k h_k * w_j * mu(k, j),   h_k = pi_{(k - l) mod N} * u_k / r'_k,
+// where r'_k = u_k sum_j w_j mu(k, j) is the row sum of row (k - l) mod N.
+// The roll J_l of Sec. 3.4 is therefore only an index rotation when h is
+// formed; no permuted copy of anything is made.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spl_device.cuh"
+#include "spl_kernels.h"
+
+namespace spl {
+
+// ======================================================================
+// Dense triangle passes (the regenerated-matrix inner loops, K4)
+// ======================================================================
+//
+// A thread owns C consecutive outputs a0..a0+C-1 inside a warp span
+// [base, base + 32 C).  Over the input index b the triangle weight is
+// uniform outside the span, so the loop splits into a "below" region
+// b < base, the 32C-wide band and an "above" region b >= base + 32C; only
+// the band needs a per-entry select.  Every entry costs one FFMA:
+// acc_c += v_b * m_c(b) with the regenerated factor m_c(b).  Sums are
+// blocked: 128-term inner chains added into an outer accumulator.
+
+constexpr int kChain = 128;
+
+// Compensated accumulation of a positive chunk sum x into (acc, comp):
+// TwoSum gives the exact rounding error of acc + x, which is carried in comp.
+__device__ __forceinline__ void two_sum_acc(float &acc, float &comp, float x) {
+    const float s = acc + x;
+    const float bb = s - acc;
+    const float e = (acc - (s - bb)) + (x - bb);
+    acc = s;
+    comp += e;
+}
+
+// Uniform-weight run over b in [lo, hi) (multiples of 4).  Each kChain-long
+// chunk is summed as four interleaved FFMA chains (one per float4 lane),
+// which are then added into the compensated outer accumulator.  Relative
+// rounding error per output ~1 FP32 unit roundoff instead of ~15 for one
+// sequential 2000-term chain.
+template <int C>
+__device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
+                                        float (&acc)[C], float (&comp)[C]) {
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    for (int b0 = lo; b0 < hi; b0 += kChain) {
+        const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
+        float i0[C], i1[C], i2[C], i3[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
+#pragma unroll 8
+        for (int q = 0; q < q1; ++q) {
+            const float4 x = v4[(b0 >> 2) + q];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                i0[c] = fmaf(x.x, m[c], i0[c]);
+                i1[c] = fmaf(x.y, m[c], i1[c]);
+                i2[c] = fmaf(x.z, m[c], i2[c]);
+                i3[c] = fmaf(x.w, m[c], i3[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
+    }
+}
+
+// Column pass: out_c = sum_b v_b * (b <= a_c ? mlo_c : mhi_c)
+//   (power step: v = h, mlo = w_j, mhi = w_j eL).
+// Row pass:    out_c = sum_b v_b * (b >= a_c ? mlo_c : mhi_c)
+//   (row sums:  v = w, mlo = u_k, mhi = u_k eL).
+// b runs over [b_lo, b_hi); v is indexed by b (callers offset the pointer
+// for a chunk).  base is the warp span start, a0 = base + lane * C.  All
+// bounds are multiples of 4; the 32C-wide span lies either fully inside
+// [b_lo, b_hi) or fully outside it.
+template <int C, bool kRowPass>
+__device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int a0,
+                                         const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
+    float acc[C], comp[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) { acc[c] = 0.f; comp[c] = 0.f; }
+    const int span_end = base + 32 * C;
+    // below the span: b < a for every owned a
+    {
+        float m[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) m[c] = kRowPass ? mhi[c] : mlo[c];
+        tri_run<C>(v, b_lo, min(b_hi, base), m, acc, comp);
+    }
+    // the span itself: per-entry select
+    {
+        const int lo = max(b_lo, base), hi = min(b_hi, span_end);
+        const float4 *v4 = reinterpret_cast<const float4 *>(v);
+        for (int b0 = lo; b0 < hi; b0 += kChain) {
+            const int b1 = min(hi, b0 + kChain);
+            float i0[C], i1[C], i2[C], i3[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
+            for (int b = b0; b < b1; b += 4) {
+                const float4 x = v4[b >> 2];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int a = a0 + c;
+                    if (kRowPass) {
+                        i0[c] = fmaf(x.x, (b + 0 >= a) ? mlo[c] : mhi[c], i0[c]);
+                        i1[c] = fmaf(x.y, (b + 1 >= a) ? mlo[c] : mhi[c], i1[c]);
+                        i2[c] = fmaf(x.z, (b + 2 >= a) ? mlo[c] : mhi[c], i2[c]);
+                        i3[c] = fmaf(x.w, (b + 3 >= a) ? mlo[c] : mhi[c], i3[c]);
+                    } else {
+                        i0[c] = fmaf(x.x, (b + 0 <= a) ? mlo[c] : mhi[c], i0[c]);
+                        i1[c] = fmaf(x.y, (b + 1 <= a) ? mlo[c] : mhi[c], i1[c]);
+                        i2[c] = fmaf(x.z, (b + 2 <= a) ? mlo[c] : mhi[c], i2[c]);
+                        i3[c] = fmaf(x.w, (b + 3 <= a) ? mlo[c] : mhi[c], i3[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
+        }
+    }
+    // above the span: b > a for every owned a
+    {
+        float m[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) m[c] = kRowPass ? mlo[c] : mhi[c];
+        tri_run<C>(v, max(b_lo, span_end), b_hi, m, acc, comp);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[c] = acc[c] + comp[c];
+}
+
+// Rounds n up to a multiple of the pass chain (and of 32C for the spans).
+__host__ __device__ __forceinline__ int pad_len(int n, int C) {
+    const int q = 32 * C > kChain ? 32 * C : kChain;
+    return (n + q - 1) / q * q;
+}
+
+// ======================================================================
+// K5: persistent batch driver with the per-CTA matrix-free step
+// ======================================================================
+//
+// One CTA processes one pixel at a time, taking pixels from an atomic work
+// queue (the host orders them by decreasing N).  Per pixel:
+//   K1    u_k, w_j (FP64 flux -> FP32 factors), eL, Lambda
+//   rows  r'_k by the dense row pass, stored as rho_k = u_k / r'_k
+//   start pi = uniform, or normalised warm weights, or softmax of logits
+//   loop  h_k = pi_{(k-l) mod N} rho_k;  y = dense column pass;
+//         pi' = y / sum(y); statistics; stop rule
+// Shared memory: v (the broadcast vector), pi, rho: 3 * Npad floats.
+// Per-CTA global scratch: w, u, y, d1, d2 (5 * Npad floats).
+
+template <int NT, int C>
+__global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
+    extern __shared__ float4 smem4[];
+    float *sv = reinterpret_cast<float *>(smem4);
+    float *spi = sv + a.npad_max;
+    float *srho = spi + a.npad_max;
+    __shared__ float red[8 * (NT / 32) + 8];
+    __shared__ int s_item;
+    __shared__ float s_scal[4];
+
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float *gw = a.scratch + (size_t)blockIdx.x * 5 * a.npad_max;
+    float *gu = gw + a.npad_max;
+    float *gy = gu + a.npad_max;
+    float *gd1 = gy + a.npad_max;
+    float *gd2 = gd1 + a.npad_max;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n) break;
+        const PixelDev p = a.px[item];
+        const int N = p.N, l = p.l;
+        const int64_t off = a.offsets ? a.offsets[p.index] : p.out_off;
+        const int npad = pad_len(N, C);
+        const int span = NT * C;                 // outputs per group
+        const int ngroups = (N + span - 1) / span;
+
+        // ---- K1: factors (FP64 inside), Lambda, eL
+        const FluxConst fc = flux_const(p);
+        const float eL = (float)exp(-fc.Lambda);
+        for (int j = tid; j < npad; j += NT) {
+            float w = 0.f, u = 0.f;
+            if (j < N) factors_bin(p, fc, j, w, u);
+            sv[j] = w;      // broadcast vector of the row pass
+            gw[j] = w;
+            gu[j] = u;
+        }
+        __syncthreads();
+
+        // ---- row sums r'_k (dense row pass), rho_k = u_k / r'_k
+        for (int g = 0; g < ngroups; ++g) {
+            const int base = (g * NW + wid) * 32 * C;
+            const int a0 = base + lane * C;
+            if (base < N) {
+                float mlo[C], mhi[C], r[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float u = (a0 + c < N) ? gu[a0 + c] : 0.f;
+                    mlo[c] = u;
+                    mhi[c] = u * eL;
+                }
+                tri_pass<C, true>(sv, 0, npad, base, a0, mlo, mhi, r);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    if (a0 + c < N) srho[a0 + c] = mlo[c] / r[c];
+            }
+        }
+
+        // ---- start vector
+        float lsum = 0.f;
+        if (a.warm == nullptr) {
+            for (int j = tid; j < N; j += NT) spi[j] = 1.f / (float)N;
+        } else if (!a.warm_logits) {
+            for (int j = tid; j < N; j += NT) {
+                const float x = fmaxf(a.warm[off + j], 0.f);
+                spi[j] = x;
+                lsum += x;
+            }
+        } else {
+            float mx = -INFINITY;
+            for (int j = tid; j < N; j += NT) mx = fmaxf(mx, a.warm[off + j]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) red[wid] = mx;
+            __syncthreads();
+            if (tid == 0) {
+                float m = red[0];
+                for (int w2 = 1; w2 < NW; ++w2) m = fmaxf(m, red[w2]);
+                s_scal[0] = m;
+            }
+            __syncthreads();
+            mx = s_scal[0];
+            for (int j = tid; j < N; j += NT) {
+                const float x = __expf(a.warm[off + j] - mx);
+                spi[j] = x;
+                lsum += x;
+            }
+        }
+        if (a.warm != nullptr) {
+            const float tot = block_sum<NT>(lsum, red);
+            const bool ok = tot > 0.f && isfinite(tot);
+            const float inv = ok ? 1.f / tot : 0.f;
+            for (int j = tid; j < N; j += NT) spi[j] = ok ? spi[j] * inv : 1.f / (float)N;
+        }
+        for (int j = tid; j < N; j += NT) { gd1[j] = 0.f; gd2[j] = 0.f; }
+        __syncthreads();
+
+        // ---- power iteration
+        StopState st;
+        stop_init(st);
+        int status = ST_ENOCONV;
+        for (int it = 0; it < a.max_iter; ++it) {
+            // h_k = pi_{(k - l) mod N} * rho_k  (J_l folded into the index)
+            for (int k = tid; k < npad; k += NT) {
+                float h = 0.f;
+                if (k < N) {
+                    int i = k - l;
+                    i += (i < 0) ? N : 0;
+                    h = spi[i] * srho[k];
+                }
+                sv[k] = h;
+            }
+            __syncthreads();
+            float ysum = 0.f;
+            for (int g = 0; g < ngroups; ++g) {
+                const int base = (g * NW + wid) * 32 * C;
+                const int a0 = base + lane * C;
+                if (base < N) {
+                    float mlo[C], mhi[C], y[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float w = (a0 + c < N) ? gw[a0 + c] : 0.f;
+                        mlo[c] = w;
+                        mhi[c] = w * eL;
+                    }
+                    tri_pass<C, false>(sv, 0, npad, base, a0, mlo, mhi, y);
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        if (a0 + c < N) { gy[a0 + c] = y[c]; ysum += y[c]; }
+                }
+            }
+            const float s = block_sum<NT>(ysum, red);   // also orders gy writes before reads
+            const float inv = 1.f / s;
+            float stats[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int j = tid; j < N; j += NT) {
+                const float pn = gy[j] * inv;
+                const float d = pn - spi[j];
+                const float e1 = gd1[j], e2 = gd2[j];
+                stats[0] += fabsf(d);
+                stats[1] = fmaf(d, d, stats[1]);
+                stats[2] = fmaf(d, e1, stats[2]);
+                stats[3] = fmaf(d, e2, stats[3]);
+                gd2[j] = e1;
+                gd1[j] = d;
+                spi[j] = pn;
+            }
+            block_sum_k<NT, 4>(stats, red);
+            if (stop_update(st, stats[0], stats[1], stats[2], stats[3], a.tol_err, a.min_iter)) {
+                status = ST_OK;
+                break;
+            }
+        }
+        __syncthreads();
+        // ---- output
+        for (int j = tid; j < N; j += NT) a.out[off + j] = spi[j];
+        if (tid == 0 && a.reports) {
+            ReportDev r;
+            r.iters = st.k;
+            r.status = status;
+            r.last_step_l1 = st.delta[(st.k + 7) & 7];
+            r.err_bound = st.err;
+            r.lambda2_abs = st.rho;
+            r.lambda2_phase = st.theta;
+            a.reports[p.index] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// ======================================================================
+// K1 for a single chain: per-bin vectors
+// ======================================================================
+
+__global__ void chain_flux_kernel(PixelDev p, float *__restrict__ w, float *__restrict__ u,
+                                  float *__restrict__ lam_out, double *__restrict__ F_out,
+                                  double *__restrict__ scal /* [0]=Lambda [1]=eL */, int npad) {
+    const FluxConst fc = flux_const(p);
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npad; j += stride) {
+        if (j < p.N) {
+            double F, lam;
+            flux_bin(p, fc, j, F, lam);
+            const double e = exp(0.5 * fc.Lambda - F);
+            w[j] = (float)(lam * e);
+            u[j] = (float)(1.0 / e);
+            if (lam_out) lam_out[j] = (float)lam;
+            if (F_out) F_out[j] = F;
+        } else {
+            w[j] = 0.f;
+            u[j] = 0.f;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[0] = fc.Lambda;
+        scal[1] = exp(-fc.Lambda);
+    }
+}
+
+// ======================================================================
+// K2: materialised build with the roll in the row address
+// ======================================================================
+//
+// One warp per row i (grid-stride).  p = (i + l) mod N selects the row
+// factor u_p: row i of E = J_l E_base is row p of E_base, read in place.
+// P_ij = u_p * w_j * (p > j ? eL : 1) with 16-byte stores; the row sum is
+// accumulated in 128-term chains and warp-reduced.
+
+__global__ void __launch_bounds__(256) build_matrix_kernel(int N, int l, int ld, const float *__restrict__ w,
+                                                           const float *__restrict__ u,
+                                                           const double *__restrict__ scal,
+                                                           float *__restrict__ P, float *__restrict__ rowsum) {
+    const float eL = (float)scal[1];
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const bool vec = (N & 3) == 0;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
+        int p = i + l;
+        p -= (p >= N) ? N : 0;
+        const float up = u[p];
+        const float upe = up * eL;
+        float *row = P + (size_t)i * ld;
+        float acc = 0.f, comp = 0.f, in = 0.f;
+        int cnt = 0;
+        if (vec) {
+            const float4 *w4 = reinterpret_cast<const float4 *>(w);
+            float4 *r4 = reinterpret_cast<float4 *>(row);
+            for (int q = lane; q < (N >> 2); q += 32) {
+                const float4 x = w4[q];
+                const int j = q << 2;
+                float4 o;
+                o.x = x.x * ((p > j) ? upe : up);
+                o.y = x.y * ((p > j + 1) ? upe : up);
+                o.z = x.z * ((p > j + 2) ? upe : up);
+                o.w = x.w * ((p > j + 3) ? upe : up);
+                __stcs(r4 + q, o);
+                in += (o.x + o.y) + (o.z + o.w);
+                if (++cnt == kChain / 4) { two_sum_acc(acc, comp, in); in = 0.f; cnt = 0; }
+            }
+        } else {
+            for (int j = lane; j < N; j += 32) {
+                const float o = w[j] * ((p > j) ? upe : up);
+                __stcs(row + j, o);
+                in += o;
+                if (++cnt == kChain) { two_sum_acc(acc, comp, in); in = 0.f; cnt = 0; }
+            }
+        }
+        two_sum_acc(acc, comp, in);
+        acc += comp;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) rowsum[i] = acc;
+    }
+}
+
+// ======================================================================
+// K3: TMA-staged GEMV over the materialised P (HBM-bound)
+// ======================================================================
+//
+// Work unit = one 32-row x 128-column tile (16 KB).  Tiles are numbered
+// slab-major (slab = 128 columns) and each CTA takes one contiguous range of
+// tiles, so every CTA streams the same number of bytes.  A single thread
+// issues cp.async.bulk.tensor.2d loads into a ring of STAGES shared-memory
+// buffers, each guarded by an mbarrier with an expected transaction count;
+// the 128 threads of the CTA each own one column of the slab and accumulate
+// c_i * P_ij down the rows (c_i = pi_i / r_i), in 32-term chains per tile.
+// A CTA's range spans at most two slabs; the partial column sums of each are
+// written to part[cta][slot][128] and reduced in fixed order by the finish
+// kernel (deterministic, no atomics).
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+constexpr int kGemvCols = 128;
+constexpr int kGemvRows = 32;
+constexpr int kGemvTileBytes = kGemvCols * kGemvRows * 4;
+
+template <int STAGES>
+__global__ void __launch_bounds__(kGemvCols) gemv_tma_kernel(const __grid_constant__ CUtensorMap tmap, GemvArgs a) {
+    extern __shared__ __align__(1024) uint8_t gsm[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[STAGES];
+    if (a.state && a.state->done) return;
+
+    const int tid = threadIdx.x;
+    const int per = a.tiles_per_cta;
+    const int t0 = blockIdx.x * per;
+    const int t1 = min(a.total_tiles, t0 + per);
+    const int ntiles = t1 - t0;
+    if (ntiles <= 0) return;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int it) {
+        const int t = t0 + it;
+        const int slab = t / a.tiles_per_slab;
+        const int rt = t - slab * a.tiles_per_slab;
+        const int s = it % STAGES;
+        mbar_expect_tx(&full[s], kGemvTileBytes);
+        tma_load_2d(tiles + (size_t)s * kGemvTileBytes, &tmap, &full[s], slab * kGemvCols, rt * kGemvRows);
+    };
+    if (tid == 0) {
+        for (int it = 0; it < STAGES && it < ntiles; ++it) issue(it);
+    }
+    const int slab0 = t0 / a.tiles_per_slab;
+    int cur_slab = slab0;
+    float acc = 0.f, comp = 0.f;
+    bool timed_out = false;
+    int it = 0;
+    for (; it < ntiles; ++it) {
+        const int s = it % STAGES;
+        const uint32_t parity = (uint32_t)((it / STAGES) & 1);
+        if (!mbar_wait(&full[s], parity)) { timed_out = true; break; }
+        const int t = t0 + it;
+        const int slab = t / a.tiles_per_slab;
+        const int rt = t - slab * a.tiles_per_slab;
+        if (slab != cur_slab) {
+            a.part[((size_t)blockIdx.x * 2 + (cur_slab - slab0)) * kGemvCols + tid] = acc + comp;
+            acc = 0.f;
+            comp = 0.f;
+            cur_slab = slab;
+        }
+        const float *tile = reinterpret_cast<const float *>(tiles + (size_t)s * kGemvTileBytes);
+        const int r0 = rt * kGemvRows;
+        float in0 = 0.f, in1 = 0.f;
+#pragma unroll
+        for (int r = 0; r < kGemvRows; r += 2) {
+            const int i = r0 + r;
+            const float c0 = (i < a.N) ? __ldg(a.c + i) : 0.f;
+            const float c1 = (i + 1 < a.N) ? __ldg(a.c + i + 1) : 0.f;
+            in0 = fmaf(c0, tile[r * kGemvCols + tid], in0);
+            in1 = fmaf(c1, tile[(r + 1) * kGemvCols + tid], in1);
+        }
+        two_sum_acc(acc, comp, in0 + in1);
+        __syncthreads();   // every thread is done with buffer s
+        if (tid == 0 && it + STAGES < ntiles) issue(it + STAGES);
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            atomicExch(a.err_flag, 1);
+            // drain copies still in flight into this CTA's buffers (bounded)
+            const int issued = min(ntiles, it + STAGES);
+            for (int k = it; k < issued; ++k) mbar_wait(&full[k % STAGES], (uint32_t)((k / STAGES) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    a.part[((size_t)blockIdx.x * 2 + (cur_slab - slab0)) * kGemvCols + tid] = acc + comp;
+}
+
+// ======================================================================
+// K4 for one large chain: column pass split over CTAs
+// ======================================================================
+//
+// Grid (column tiles) x (b-chunks).  Each CTA copies its chunk of the
+// broadcast vector v into shared memory and runs the dense triangle pass for
+// its columns over that chunk only; partial sums go to part[chunk][col].
+
+template <int NT, int C, bool kRowPass>
+__global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float *sv = reinterpret_cast<float *>(smem4);
+    if (a.state && a.state->done) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int cols_per_cta = NT * C;
+    const int col0 = blockIdx.x * cols_per_cta;
+    const int b0 = blockIdx.y * a.chunk;
+    const int b1 = min(a.vlen, b0 + a.chunk);
+    const int blen = b1 - b0;                 // multiple of kChain
+    for (int b = tid; b < blen; b += NT) sv[b] = a.v[b0 + b];
+    __syncthreads();
+    const int a0 = col0 + (wid * 32 + lane) * C;
+    const int wbase = col0 + wid * 32 * C;
+    if (wbase >= a.N) return;
+    const float eL = (float)a.scal[1];
+    float mlo[C], mhi[C], out[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float m = (a0 + c < a.N) ? a.m[a0 + c] : 0.f;
+        mlo[c] = m;
+        mhi[c] = m * eL;
+    }
+    tri_pass<C, kRowPass>(sv - b0, b0, b1, wbase, a0, mlo, mhi, out);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        if (a0 + c < a.N) a.part[(size_t)blockIdx.y * a.ld_part + a0 + c] = out[c];
+}
+
+// ======================================================================
+// Finish kernel of one power step (single CTA)
+// ======================================================================
+//
+// Reduces the partial column sums into y, normalises, forms the step
+// statistics, applies the stop rule, and prepares the next broadcast vector:
+//   materialised: c_i = pi_i / r_i           (row space)
+//   fused:        h_k = pi_{(k-l) mod N} rho_k  (p-space)
+
+template <int NT>
+__global__ void __launch_bounds__(NT) finish_step_kernel(FinishArgs a) {
+    __shared__ float red[8 * (NT / 32) + 8];
+    ChainState *stp = a.state;
+    if (stp->done) return;
+    const int N = a.N;
+    const int tid = threadIdx.x;
+    float ysum = 0.f;
+    for (int j = tid; j < N; j += NT) {
+        float y = 0.f;
+        if (a.mode == 0) {
+            // materialised: partials per (cta, slot)
+            const int slab = j / kGemvCols, t = j - slab * kGemvCols;
+            const int lo = slab * a.tiles_per_slab, hi = lo + a.tiles_per_slab - 1;
+            const int c_lo = lo / a.tiles_per_cta, c_hi = hi / a.tiles_per_cta;
+            for (int c = c_lo; c <= c_hi; ++c) {
+                const int slot = slab - (c * a.tiles_per_cta) / a.tiles_per_slab;
+                y += a.part[((size_t)c * 2 + slot) * kGemvCols + t];
+            }
+        } else {
+            for (int q = 0; q < a.nparts; ++q) y += a.part[(size_t)q * a.ld_part + j];
+        }
+        a.y[j] = y;
+        ysum += y;
+    }
+    const float s = block_sum<NT>(ysum, red);
+    const float inv = 1.f / s;
+    float stats[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = tid; j < N; j += NT) {
+        const float pn = a.y[j] * inv;
+        const float d = pn - a.pi[j];
+        const float e1 = a.d1[j], e2 = a.d2[j];
+        stats[0] += fabsf(d);
+        stats[1] = fmaf(d, d, stats[1]);
+        stats[2] = fmaf(d, e1, stats[2]);
+        stats[3] = fmaf(d, e2, stats[3]);
+        a.d2[j] = e1;
+        a.d1[j] = d;
+        a.pi[j] = pn;
+    }
+    block_sum_k<NT, 4>(stats, red);
+    StopState st = stp->st;
+    const bool stop = stop_update(st, stats[0], stats[1], stats[2], stats[3], stp->tol_err, stp->min_iter);
+    __syncthreads();
+    if (tid == 0) {
+        stp->st = st;
+        if (stop) { stp->done = 1; stp->status = ST_OK; }
+        else if (st.k >= stp->max_iter) { stp->done = 1; stp->status = ST_ENOCONV; }
+    }
+    if (stop) return;
+    // next broadcast vector
+    for (int k = tid; k < a.vlen; k += NT) {
+        float h = 0.f;
+        if (k < N) {
+            if (a.mode == 0) {
+                h = a.pi[k] / a.rowsum[k];
+            } else {
+                int i = k - a.l;
+                i += (i < 0) ? N : 0;
+                h = a.pi[i] * a.rho[k];
+            }
+        }
+        a.v[k] = h;
+    }
+}
+
+// Start of an iteration: pi = uniform or normalised warm weights; stop state
+// reset; first broadcast vector.
+template <int NT>
+__global__ void __launch_bounds__(NT) init_iter_kernel(FinishArgs a, const float *__restrict__ warm) {
+    __shared__ float red[8 * (NT / 32) + 8];
+    const int N = a.N, tid = threadIdx.x;
+    float ls = 0.f;
+    for (int j = tid; j < N; j += NT) {
+        const float x = warm ? fmaxf(warm[j], 0.f) : 1.f;
+        a.pi[j] = x;
+        ls += x;
+        a.d1[j] = 0.f;
+        a.d2[j] = 0.f;
+    }
+    const float s = block_sum<NT>(ls, red);
+    const bool ok = s > 0.f && isfinite(s);
+    for (int j = tid; j < N; j += NT) a.pi[j] = ok ? a.pi[j] / s : 1.f / (float)N;
+    __syncthreads();
+    for (int k = tid; k < a.vlen; k += NT) {
+        float h = 0.f;
+        if (k < N) {
+            if (a.mode == 0) {
+                h = a.pi[k] / a.rowsum[k];
+            } else {
+                int i = k - a.l;
+                i += (i < 0) ? N : 0;
+                h = a.pi[i] * a.rho[k];
+            }
+        }
+        a.v[k] = h;
+    }
+    if (tid == 0) {
+        StopState st;
+        stop_init(st);
+        a.state->st = st;
+        a.state->done = 0;
+        a.state->status = ST_ENOCONV;
+    }
+}
+
+// rho_k = u_k / r'_k from the split row pass partials; also the row sums of
+// the paper's P for inspection.
+template <int NT>
+__global__ void __launch_bounds__(NT) finish_rows_kernel(int N, int nparts, int ld_part,
+                                                         const float *__restrict__ part,
+                                                         const float *__restrict__ u, float *__restrict__ rho,
+                                                         float *__restrict__ rowsum_p, int l) {
+    for (int k = blockIdx.x * NT + threadIdx.x; k < N; k += gridDim.x * NT) {
+        float r = 0.f;
+        for (int q = 0; q < nparts; ++q) r += part[(size_t)q * ld_part + k];
+        rho[k] = u[k] / r;
+        // row i = (k - l) mod N of P has sum r'_k
+        int i = k - l;
+        i += (i < 0) ? N : 0;
+        if (rowsum_p) rowsum_p[i] = r;
+    }
+}
+
+// ======================================================================
+// Launchers
+// ======================================================================
+
+int batch_threads_for(int nmax) { return nmax <= 2048 ? 512 : 1024; }
+
+cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
+    if (threads == 512) {
+        auto k = batch_fused_kernel<512, 4>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 512, smem, s>>>(a);
+    } else if (threads == 256) {
+        auto k = batch_fused_kernel<256, 4>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 256, smem, s>>>(a);
+    } else {
+        auto k = batch_fused_kernel<1024, 4>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 1024, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int NT>
+static cudaError_t occupancy_one(size_t smem, int *bps) {
+    auto k = batch_fused_kernel<NT, 4>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, smem);
+}
+
+cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm) {
+    if (threads == 512) return occupancy_one<512>(smem, blocks_per_sm);
+    if (threads == 256) return occupancy_one<256>(smem, blocks_per_sm);
+    return occupancy_one<1024>(smem, blocks_per_sm);
+}
+
+int batch_pad_len(int n) { return pad_len(n, 4); }
+
+cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal, int npad,
+                              cudaStream_t s) {
+    const int threads = 256;
+    int blocks = (npad + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    chain_flux_kernel<<<blocks, threads, 0, s>>>(p, w, u, lam, F, scal, npad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_matrix(int N, int l, int ld, const float *w, const float *u, const double *scal, float *P,
+                                float *rowsum, int num_sms, cudaStream_t s) {
+    int blocks = num_sms * 8;
+    const int need = (N + 7) / 8;
+    if (blocks > need) blocks = need;
+    build_matrix_kernel<<<blocks, 256, 0, s>>>(N, l, ld, w, u, scal, P, rowsum);
+    return cudaGetLastError();
+}
+
+constexpr int kGemvStages = 8;
+
+size_t gemv_smem_bytes() { return (size_t)kGemvStages * kGemvTileBytes + 1024; }
+
+cudaError_t launch_gemv(const CUtensorMap *map, const GemvArgs &a, int grid, cudaStream_t s) {
+    auto k = gemv_tma_kernel<kGemvStages>;
+    const size_t smem = gemv_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kGemvCols, smem, s>>>(*map, a);
+    return cudaGetLastError();
+}
+
+constexpr int kSplitNT = 128;
+constexpr int kSplitC = 4;
+
+int split_cols_per_cta() { return kSplitNT * kSplitC; }
+int split_pad_len(int n) { return pad_len(n, kSplitC); }
+
+cudaError_t launch_tri_split(const TriSplitArgs &a, bool row_pass, int chunks, cudaStream_t s) {
+    const int cols = kSplitNT * kSplitC;
+    dim3 grid((a.N + cols - 1) / cols, chunks);
+    const size_t smem = (size_t)a.chunk * sizeof(float);
+    cudaError_t e;
+    if (row_pass) {
+        auto k = tri_split_kernel<kSplitNT, kSplitC, true>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kSplitNT, smem, s>>>(a);
+    } else {
+        auto k = tri_split_kernel<kSplitNT, kSplitC, false>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kSplitNT, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_rows(int N, int nparts, int ld_part, const float *part, const float *u, float *rho,
+                               float *rowsum_p, int l, cudaStream_t s) {
+    int blocks = (N + 255) / 256;
+    finish_rows_kernel<256><<<blocks, 256, 0, s>>>(N, nparts, ld_part, part, u, rho, rowsum_p, l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_step(const FinishArgs &a, cudaStream_t s) {
+    finish_step_kernel<1024><<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_iter(const FinishArgs &a, const float *warm, cudaStream_t s) {
+    init_iter_kernel<1024><<<1, 1024, 0, s>>>(a, warm);
+    return cudaGetLastError();
+}
+
+}  // namespace spl

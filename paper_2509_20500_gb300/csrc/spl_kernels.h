@@ -1,0 +1,98 @@
+// Internal interface between the libspl host code and its kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spl_device.cuh"
+
+namespace spl {
+
+// Device-resident state of one chain's iteration (single-pixel API).
+struct ChainState {
+    StopState st;
+    int32_t done;
+    int32_t status;
+    float tol_err;
+    int32_t max_iter;
+    int32_t min_iter;
+    int32_t pad_[3];
+};
+
+struct BatchArgs {
+    const PixelDev *px;      // sorted work list
+    int n;
+    int *counter;            // work-queue head, zero before launch
+    const float *warm;       // NULL, packed weights, or packed logits
+    int warm_logits;
+    float *out;              // packed output
+    const int64_t *offsets;  // [n + 1] caller offsets by caller index, or NULL (use px.out_off)
+    ReportDev *reports;      // [n] by caller index, may be NULL
+    float *scratch;          // [grid][5][npad_max]
+    int npad_max;
+    float tol_err;
+    int max_iter;
+    int min_iter;
+};
+
+struct GemvArgs {
+    int N;
+    int tiles_per_slab;      // ceil(N / 32)
+    int total_tiles;         // slabs * tiles_per_slab
+    int tiles_per_cta;
+    const float *c;          // [N] row coefficients pi_i / r_i
+    float *part;             // [grid][2][128]
+    const ChainState *state; // early exit once converged (may be NULL)
+    int *err_flag;
+};
+
+struct TriSplitArgs {
+    int N;
+    int vlen;                // padded length of v (multiple of 128)
+    int chunk;               // b-chunk per CTA row (multiple of 128)
+    const float *v;          // broadcast vector [vlen]
+    const float *m;          // per-output factor: w (column pass) or u (row pass)
+    const double *scal;      // [0] Lambda, [1] eL
+    float *part;             // [chunks][ld_part]
+    int ld_part;
+    const ChainState *state; // may be NULL
+};
+
+struct FinishArgs {
+    int mode;                // 0 materialised (GEMV partials), 1 fused (split partials)
+    int N, l;
+    int vlen;
+    // materialised partial layout
+    int tiles_per_slab, tiles_per_cta;
+    // fused partial layout
+    int nparts, ld_part;
+    const float *part;
+    float *y, *pi, *d1, *d2;
+    const float *rowsum;     // materialised: r_i
+    const float *rho;        // fused: u_k / r'_k
+    float *v;                // next broadcast vector
+    ChainState *state;
+};
+
+int batch_threads_for(int nmax);
+int batch_pad_len(int n);
+cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);
+
+cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal,
+                              int npad, cudaStream_t s);
+cudaError_t launch_build_matrix(int N, int l, int ld, const float *w, const float *u, const double *scal, float *P,
+                                float *rowsum, int num_sms, cudaStream_t s);
+size_t gemv_smem_bytes();
+cudaError_t launch_gemv(const CUtensorMap *map, const GemvArgs &a, int grid, cudaStream_t s);
+
+int split_cols_per_cta();
+int split_pad_len(int n);
+cudaError_t launch_tri_split(const TriSplitArgs &a, bool row_pass, int chunks, cudaStream_t s);
+cudaError_t launch_finish_rows(int N, int nparts, int ld_part, const float *part, const float *u, float *rho,
+                               float *rowsum_p, int l, cudaStream_t s);
+cudaError_t launch_finish_step(const FinishArgs &a, cudaStream_t s);
+cudaError_t launch_init_iter(const FinishArgs &a, const float *warm, cudaStream_t s);
+
+}  // namespace spl

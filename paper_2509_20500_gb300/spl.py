@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libspl (include/spl.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (passed by data pointer with
+the current torch stream); host buffers are NumPy arrays.  The library must
+have been built (``paper_2509_20500_gb300.build.build()``); a missing library
+raises ImportError rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspl.so")
+
+SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ENOCONV, SPL_ETIMEOUT = range(6)
+SPL_MATERIALIZED, SPL_FUSED = 0, 1
+
+
+class spl_pixel_t(ctypes.Structure):
+    _fields_ = [("t_r", ctypes.c_double), ("t_d", ctypes.c_double), ("tau", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("S", ctypes.c_double), ("B", ctypes.c_double),
+                ("n_bins", ctypes.c_int32), ("shift_override", ctypes.c_int32)]
+
+
+class spl_report_t(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("last_step_l1", ctypes.c_float),
+                ("err_bound", ctypes.c_float), ("lambda2_abs", ctypes.c_float),
+                ("lambda2_phase", ctypes.c_float)]
+
+
+class spl_batch_opts_t(ctypes.Structure):
+    _fields_ = [("warm_is_logits", ctypes.c_int32), ("min_iter", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32)]
+
+
+REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_l1", np.float32),
+                         ("err_bound", np.float32), ("lambda2_abs", np.float32),
+                         ("lambda2_phase", np.float32)])
+
+# Symbols include/spl.h declares (checked by the CPU tests).
+EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_stationary_ex", "spl_batch_kernel_ms",
+            "spl_batch_stationary_host", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
+            "spl_last_cuda_error", "spl_version"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SplError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().spl_strerror(status).decode()
+        if status == SPL_ECUDA:
+            msg += f" ({lib().spl_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {msg}")
+
+
+def lib():
+    """Load libspl (raises ImportError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libspl is not built ({LIB_PATH} missing); run paper_2509_20500_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        L.spl_build.argtypes = [ctypes.POINTER(spl_pixel_t), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.spl_build.restype = ctypes.c_int
+        L.spl_stationary.argtypes = [vp, f64, i32, vp, vp, ctypes.POINTER(spl_report_t)]
+        L.spl_stationary.restype = ctypes.c_int
+        L.spl_batch_stationary.argtypes = [ctypes.POINTER(spl_pixel_t), i32, f64, i32, vp, vp, vp,
+                                           ctypes.POINTER(spl_report_t), vp]
+        L.spl_batch_stationary.restype = ctypes.c_int
+        L.spl_batch_stationary_ex.argtypes = [ctypes.POINTER(spl_pixel_t), i32, f64, i32, vp, vp, vp,
+                                              ctypes.POINTER(spl_report_t), vp,
+                                              ctypes.POINTER(spl_batch_opts_t)]
+        L.spl_batch_stationary_ex.restype = ctypes.c_int
+        L.spl_batch_stationary_host.argtypes = [ctypes.POINTER(spl_pixel_t), i32, f64, i32, vp, vp,
+                                                ctypes.POINTER(spl_report_t), vp]
+        L.spl_batch_stationary_host.restype = ctypes.c_int
+        L.spl_batch_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
+        L.spl_batch_kernel_ms.restype = ctypes.c_int
+        L.spl_matrix.argtypes = [vp, vp]
+        L.spl_matrix.restype = ctypes.c_int
+        L.spl_chain_flux.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        L.spl_chain_flux.restype = ctypes.c_int
+        L.spl_free.argtypes = [vp]
+        L.spl_free.restype = None
+        L.spl_strerror.argtypes = [ctypes.c_int]
+        L.spl_strerror.restype = ctypes.c_char_p
+        L.spl_last_cuda_error.argtypes = []
+        L.spl_last_cuda_error.restype = ctypes.c_char_p
+        L.spl_version.argtypes = []
+        L.spl_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(st: int, where: str, allow=(SPL_OK,)):
+    if st not in allow:
+        raise SplError(st, where)
+    return st
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pixels_to_c(px: np.ndarray):
+    """Marshal a workloads.PIXEL_DTYPE array into a ctypes spl_pixel_t array."""
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    arr = (spl_pixel_t * max(1, len(px)))()
+    ctypes.memmove(arr, px.ctypes.data, px.nbytes)
+    return arr
+
+
+def offsets_of(px: np.ndarray) -> np.ndarray:
+    off = np.zeros(len(px) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(px["n_bins"].astype(np.int64))
+    return off
+
+
+def _reports_np(reps, n):
+    out = np.zeros(n, dtype=REPORT_DTYPE)
+    if n:
+        ctypes.memmove(out.ctypes.data, reps, out.nbytes)
+    return out
+
+
+class Chain:
+    """One built pixel chain (spl_build ... spl_free)."""
+
+    def __init__(self, pixel: np.ndarray, mode: int = SPL_FUSED, stream=None):
+        self._c = ctypes.c_void_p()
+        self.n_bins = int(np.asarray(pixel)["n_bins"].reshape(-1)[0])
+        arr = pixels_to_c(np.asarray(pixel).reshape(-1)[:1])
+        self.mode = mode
+        self._stream = _stream_ptr(stream)
+        _check(lib().spl_build(arr, mode, self._stream, ctypes.byref(self._c)), "spl_build")
+
+    def stationary(self, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None, allow_noconv=False):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_bins, dtype=torch.float32, device="cuda")
+        rep = spl_report_t()
+        allow = (SPL_OK, SPL_ENOCONV) if allow_noconv else (SPL_OK,)
+        st = lib().spl_stationary(self._c, float(tol), int(max_iter), _dptr(warm), _dptr(out), ctypes.byref(rep))
+        _check(st, "spl_stationary", allow)
+        return out, _reports_np(ctypes.addressof(rep), 1)[0]
+
+    def matrix(self):
+        import torch
+        P = torch.empty((self.n_bins, self.n_bins), dtype=torch.float32, device="cuda")
+        _check(lib().spl_matrix(self._c, _dptr(P)), "spl_matrix")
+        return P
+
+    def flux(self):
+        import torch
+        lam = torch.empty(self.n_bins, dtype=torch.float32, device="cuda")
+        F = torch.empty(self.n_bins, dtype=torch.float64, device="cuda")
+        Lam = ctypes.c_double()
+        sh = ctypes.c_int32()
+        _check(lib().spl_chain_flux(self._c, _dptr(lam), _dptr(F), ctypes.byref(Lam), ctypes.byref(sh)),
+               "spl_chain_flux")
+        return lam, F, Lam.value, sh.value
+
+    def close(self):
+        if self._c:
+            lib().spl_free(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
+                     warm_is_logits: bool = False, min_iter: int = 1, threads: int = 0, reports: bool = True,
+                     offsets=None, stream=None, time_kernel: bool = False, c_pixels=None):
+    """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
+    import torch
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    n = len(px)
+    off = offsets_of(px)
+    if offsets is None:
+        offsets = torch.from_numpy(off).to("cuda")
+    if out is None:
+        out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
+    arr = pixels_to_c(px) if c_pixels is None else c_pixels
+    reps = (spl_report_t * max(1, n))() if reports else None
+    opts = spl_batch_opts_t(int(bool(warm_is_logits)), int(min_iter), int(threads), int(bool(time_kernel)))
+    st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
+                                       reps, _stream_ptr(stream), ctypes.byref(opts))
+    _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
+    return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def batch_kernel_ms() -> float:
+    """Device time of the batch kernel of the last call made with time_kernel=True."""
+    ms = ctypes.c_float()
+    _check(lib().spl_batch_kernel_ms(ctypes.byref(ms)), "spl_batch_kernel_ms")
+    return float(ms.value)
+
+
+def batch_stationary_host(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm: np.ndarray | None = None,
+                          out: np.ndarray | None = None, reports: bool = True, stream=None):
+    """spl_batch_stationary_host: host buffers in and out (copies inside the call)."""
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    n = len(px)
+    off = offsets_of(px)
+    if out is None:
+        out = np.empty(int(off[-1]), dtype=np.float32)
+    arr = pixels_to_c(px)
+    reps = (spl_report_t * max(1, n))() if reports else None
+    wp = None if warm is None else ctypes.c_void_p(np.ascontiguousarray(warm, dtype=np.float32).ctypes.data)
+    st = lib().spl_batch_stationary_host(arr, n, float(tol), int(max_iter), wp, ctypes.c_void_p(out.ctypes.data),
+                                         reps, _stream_ptr(stream))
+    _check(st, "spl_batch_stationary_host", (SPL_OK, SPL_ENOCONV))
+    return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)

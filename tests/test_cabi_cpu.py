@@ -1,0 +1,92 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, exports every symbol include/spl.h declares, the struct layouts agree,
+and host-side validation rejects bad input before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2509_20500_gb300 import build, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    build.build()
+    from paper_2509_20500_gb300 import spl
+    spl.lib()
+    return spl
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "spl.h")).read()
+    return sorted(set(re.findall(r"SPL_API\s+[\w\s\*]*?\b(spl_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(S):
+    decl = declared_symbols()
+    assert len(decl) >= 11
+    L = S.lib()
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(S.EXPORTED) == decl
+
+
+def test_struct_layouts(S):
+    assert ctypes.sizeof(S.spl_pixel_t) == 56 == W.PIXEL_DTYPE.itemsize
+    assert ctypes.sizeof(S.spl_report_t) == 24 == S.REPORT_DTYPE.itemsize
+    assert ctypes.sizeof(S.spl_batch_opts_t) == 16
+
+
+def test_strerror_and_version(S):
+    L = S.lib()
+    assert L.spl_strerror(0) == b"ok"
+    assert b"converge" in L.spl_strerror(4)
+    assert b"sm_103a" in L.spl_version()
+
+
+BAD = [dict(sigma=0.0), dict(sigma=-1.0), dict(t_r=0.0), dict(t_d=-1.0), dict(S=-0.1), dict(B=-0.1),
+       dict(S=0.0, B=0.0), dict(tau=100.0), dict(tau=-0.5), dict(n_bins=1), dict(t_d=float("nan")),
+       dict(S=float("inf")), dict(S=100.0, B=30.0), dict(shift_override=-2)]
+
+
+@pytest.mark.parametrize("bad", BAD)
+def test_build_rejects_invalid_pixel_without_gpu(S, bad):
+    kw = dict(n_bins=100, t_d=75.0, tau=30.0, sigma=0.5, S=0.5, B=0.5)
+    kw.update(bad)
+    px = W.pixel(**kw)
+    out = ctypes.c_void_p()
+    st = S.lib().spl_build(S.pixels_to_c(px), S.SPL_FUSED, None, ctypes.byref(out))
+    assert st == S.SPL_EINVAL and not out.value
+
+
+def test_null_arguments_rejected(S):
+    L = S.lib()
+    out = ctypes.c_void_p()
+    assert L.spl_build(None, 0, None, ctypes.byref(out)) == S.SPL_EINVAL
+    assert L.spl_build(S.pixels_to_c(W.single()), 7, None, ctypes.byref(out)) == S.SPL_EINVAL
+    assert L.spl_stationary(None, 1e-6, 10, None, None, None) == S.SPL_EINVAL
+    assert L.spl_matrix(None, None) == S.SPL_EINVAL
+    assert L.spl_batch_stationary(None, 3, 1e-6, 10, None, None, None, None, None) == S.SPL_EINVAL
+    assert L.spl_batch_stationary(S.pixels_to_c(W.single()), 1, -1.0, 10, None, None, None, None, None) \
+        == S.SPL_EINVAL
+    L.spl_free(None)
+
+
+def test_oracle_and_library_share_nothing():
+    """The oracle sources and the CUDA sources include none of each other's
+    files, and neither Python side imports the other."""
+    csrc = os.path.join(ROOT, "paper_2509_20500_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+    otxt = open(os.path.join(ROOT, "oracle", "spl_oracle.c")).read()
+    assert "spl.h" not in otxt and "spl_device" not in otxt
+    for f in ("spl.py", "build.py", "workloads.py", "__init__.py"):
+        txt = open(os.path.join(ROOT, "paper_2509_20500_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt, f
+    ow = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert "paper_2509_20500_gb300" not in ow

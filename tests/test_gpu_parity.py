@@ -1,0 +1,284 @@
+"""GPU path (libspl through its C ABI) against the FP64 oracle.
+
+Tolerances: the stationary pmf must be within 1e-6 in L1 of the oracle's
+(the accuracy target of the method's batched form); matrix entries carry a
+few FP32 roundings of FP64-exact factors, so 1e-6 relative per entry; the
+FP64 cumulative flux is compared to 1e-12 absolute.  Row shifts and bin
+indexing are integer work and must match exactly (checked through entries
+that differ by the factor exp(-Lambda) when a row is off by one).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_20500_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L1_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def spl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_20500_gb300 import build, spl as S
+    build.build()
+    S.lib()
+    return S
+
+
+def _dict(px, k=0):
+    return W.as_dicts(px[k:k + 1])[0]
+
+
+def _l1(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).sum())
+
+
+# ---------------------------------------------------------------- K1 flux
+
+@pytest.mark.parametrize("px", [W.single(), W.pixel(2000, 75.0, 5.0, 1.0, 5.0, 0.01),
+                                W.pixel(777, 130.0, 94.5, 0.2, 0.01, 5.0)])
+def test_flux_matches_oracle(spl, px):
+    ch = spl.Chain(px, spl.SPL_FUSED)
+    lam, F, Lam, shift = ch.flux()
+    p = _dict(px)
+    N = p["n_bins"]
+    s = (np.arange(N) + 0.5) * p["t_r"] / N
+    np.testing.assert_allclose(F.cpu().numpy(), oracle.flux_F(p, s), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lam.cpu().numpy(), oracle.flux_lambda(p, s), rtol=2e-7, atol=0)
+    assert abs(Lam - oracle.Lambda(p)) < 1e-12
+    assert shift == oracle.shift_l(p) % N
+    ch.close()
+
+
+# ---------------------------------------------------------------- K2 materialised build
+
+@pytest.mark.parametrize("k", range(10))
+def test_materialized_matrix_entries(spl, k):
+    """Every entry of P vs the sequential construction (Eq. 4) with the exact
+    shift; ragged N (not multiples of 4 or 32), t_d > t_r, t_d = 0."""
+    px = W.random_small(10, seed=21, n_min=2, n_max=300)
+    p = _dict(px, k)
+    m = oracle.shift_exact(p)
+    px = px[k:k + 1].copy()
+    px["shift_override"] = m
+    ch = spl.Chain(px, spl.SPL_MATERIALIZED)
+    P = ch.matrix().cpu().numpy().astype(np.float64)
+    ref = oracle.build_seq(p) * (-math.expm1(-oracle.Lambda(p)))   # drop the constant 1/(1 - e^-Lambda)
+    np.testing.assert_allclose(P, ref, rtol=1e-6, atol=0)
+    ch.close()
+
+
+def test_materialized_matrix_paper_shift(spl):
+    """Default shift l = ceil(q) (Theorem 2) at a non-integer q with
+    frac(q) <= 1/2: entries equal the reparameterised oracle with shift l and
+    differ from the exact-shift construction by one row roll."""
+    px = W.pixel(200, 72.2, 30.0, 2.0, 1.5, 0.7)
+    p = _dict(px)
+    l = oracle.shift_l(p)
+    assert l != oracle.shift_exact(p)
+    ch = spl.Chain(px, spl.SPL_MATERIALIZED)
+    P = ch.matrix().cpu().numpy().astype(np.float64)
+    ref = oracle.build_reparam(p, l) * (-math.expm1(-oracle.Lambda(p)))
+    np.testing.assert_allclose(P, ref, rtol=1e-6, atol=0)
+    ch.close()
+
+
+# ---------------------------------------------------------------- single chain, both modes
+
+SINGLE_CASES = [
+    W.single(),
+    W.pixel(37, 75.0, 30.0, 2.0, 0.5, 0.5),
+    W.pixel(333, 130.0, 50.0, 1.0, 3.0, 6.0),
+    W.pixel(2000, 75.0, 5.0, 1.0, 5.0, 0.01),       # peaked, low background
+    W.pixel(1024, 95.0, 30.0, 0.5, 9.0, 9.0),       # high flux (paper grid corner)
+    W.pixel(2, 10.0, 30.0, 3.0, 1.0, 1.0),          # smallest chain
+]
+
+
+@pytest.mark.parametrize("mode", ["materialized", "fused"])
+@pytest.mark.parametrize("case", range(len(SINGLE_CASES)))
+def test_chain_stationary_vs_oracle(spl, mode, case):
+    px = SINGLE_CASES[case]
+    p = _dict(px)
+    ref = oracle.stationary(p, shift=oracle.shift_l(p))
+    ch = spl.Chain(px, spl.SPL_MATERIALIZED if mode == "materialized" else spl.SPL_FUSED)
+    pi, rep = ch.stationary(tol=1e-6, max_iter=500)
+    pi = pi.cpu().numpy()
+    assert rep["status"] == 0
+    assert abs(pi.sum() - 1.0) < 1e-5
+    assert _l1(pi, ref) < L1_TOL, (_l1(pi, ref), rep)
+    ch.close()
+
+
+def test_chain_integer_shift_equals_sequential(spl):
+    """Configuration with integer q: the paper's shift equals the exact one and
+    the GPU result matches Rapp's sequential construction directly."""
+    px = W.single()
+    p = _dict(px)
+    ref = oracle.stationary(p)
+    for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
+        ch = spl.Chain(px, mode)
+        pi, rep = ch.stationary(tol=1e-6)
+        assert _l1(pi.cpu().numpy(), ref) < L1_TOL
+        ch.close()
+
+
+def test_chain_max_iter_reports_noconv(spl):
+    ch = spl.Chain(W.single(), spl.SPL_FUSED)
+    pi, rep = ch.stationary(tol=1e-9, max_iter=2, allow_noconv=True)
+    assert rep["status"] == spl.SPL_ENOCONV and rep["iters"] == 2
+    ch.close()
+
+
+def test_chain_warm_start_from_answer(spl):
+    px = W.pixel(1500, 75.0, 40.0, 0.4, 2.0, 0.3)
+    p = _dict(px)
+    ref = oracle.stationary(p, shift=oracle.shift_l(p))
+    ch = spl.Chain(px, spl.SPL_FUSED)
+    warm = torch.tensor(ref * 7.0, dtype=torch.float32, device="cuda")   # unnormalised on purpose
+    pi, rep = ch.stationary(tol=1e-6, warm=warm)
+    assert rep["iters"] <= 5
+    assert _l1(pi.cpu().numpy(), ref) < L1_TOL
+    ch.close()
+
+
+@pytest.mark.parametrize("t_d", [10.0, 130.0])
+def test_highres_materialized_and_fused(spl, t_d):
+    """N = 10000 (400 MB FP32 matrix): both paths agree with the oracle."""
+    px = W.pixel(10000, t_d, 30.0, 0.3, 5.0, 0.5)
+    p = _dict(px)
+    ref = oracle.batch_stationary([p], tol=1e-12)[0]
+    for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
+        ch = spl.Chain(px, mode)
+        pi, rep = ch.stationary(tol=1e-6, max_iter=500)
+        assert rep["status"] == 0
+        assert _l1(pi.cpu().numpy(), ref) < L1_TOL
+        ch.close()
+
+
+def test_pure_background_uniform(spl):
+    px = W.pixel(999, 33.3, 30.0, 0.5, 0.0, 2.0)
+    for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
+        ch = spl.Chain(px, mode)
+        pi, rep = ch.stationary(tol=1e-6)
+        assert np.abs(pi.cpu().numpy() - 1.0 / 999).max() < 1e-9
+        ch.close()
+
+
+# ---------------------------------------------------------------- batch (K5)
+
+def test_batch_array_sample_vs_oracle(spl):
+    """128x128 array workload at N = 2000: every pixel is computed in one
+    persistent launch; 64 pixels sampled by seed are compared to the oracle."""
+    px = W.array128()
+    out, off, reps = spl.batch_stationary(px, tol=1e-6, max_iter=500)
+    torch.cuda.synchronize()
+    assert np.all(reps["status"] == 0)
+    idx = W.sample_indices(len(px), 64, seed=33)
+    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
+    o = out.cpu().numpy()
+    worst = 0.0
+    for r, k in enumerate(idx):
+        e = _l1(o[off[k]:off[k + 1]], refs[roff[r]:roff[r + 1]])
+        worst = max(worst, e)
+    assert worst < L1_TOL, worst
+    # every pmf sums to 1
+    sums = np.add.reduceat(o.astype(np.float64), off[:-1])
+    assert np.abs(sums - 1).max() < 1e-5
+
+
+def test_batch_ragged_mixed_sizes(spl):
+    """Uneven N (2 ... 4000, not multiples of the tile), t_d > t_r, t_d = 0,
+    non-integer shifts: each pixel against the reparameterised oracle with the
+    same shift l."""
+    a = W.random_small(40, seed=8, n_min=2, n_max=400)
+    b = W.uneven(12, seed=9)
+    b = b[b["n_bins"] <= 4000]
+    px = np.concatenate([a, b])
+    out, off, reps = spl.batch_stationary(px, tol=1e-6, max_iter=1000)
+    o = out.cpu().numpy()
+    for k, p in enumerate(W.as_dicts(px)):
+        ref = oracle.stationary(p, shift=oracle.shift_l(p))
+        assert reps["status"][k] == 0
+        assert _l1(o[off[k]:off[k + 1]], ref) < L1_TOL, (k, p)
+
+
+def test_batch_result_independent_of_batch(spl):
+    """A pixel's pmf does not depend on the other pixels in the launch."""
+    px = W.array_pixels(300, seed=12)
+    out, off, _ = spl.batch_stationary(px)
+    o = out.cpu().numpy()
+    for k in (0, 17, 299):
+        one, _, _ = spl.batch_stationary(px[k:k + 1])
+        np.testing.assert_array_equal(one.cpu().numpy(), o[off[k]:off[k + 1]])
+
+
+def test_batch_custom_offsets(spl):
+    """Outputs land at the caller's offsets (here with gaps and reversed order)."""
+    px = W.array_pixels(5, seed=13, n_bins=300)
+    dense, doff, _ = spl.batch_stationary(px)
+    offs = np.array([4000, 3000, 2000, 1000, 0, 5000], dtype=np.int64)
+    out = torch.full((5000,), -1.0, device="cuda")
+    spl.batch_stationary(px, out=out, offsets=torch.from_numpy(offs).cuda())
+    o, d = out.cpu().numpy(), dense.cpu().numpy()
+    for k in range(5):
+        np.testing.assert_array_equal(o[offs[k]:offs[k] + 300], d[doff[k]:doff[k + 1]])
+
+
+def test_batch_warm_logits_and_weights(spl):
+    px = W.array_pixels(32, seed=14, n_bins=500)
+    ref, off, reps0 = spl.batch_stationary(px)
+    r = ref.cpu().numpy().astype(np.float64)
+    logits = torch.tensor(np.log(r), dtype=torch.float32, device="cuda")
+    o1, _, reps1 = spl.batch_stationary(px, warm=logits, warm_is_logits=True)
+    o2, _, reps2 = spl.batch_stationary(px, warm=ref * 3.0)
+    assert reps1["iters"].max() <= 5 and reps2["iters"].max() <= 5
+    assert reps0["iters"].mean() > reps1["iters"].mean()
+    for o in (o1, o2):
+        o = o.cpu().numpy()
+        for k in range(len(px)):
+            assert _l1(o[off[k]:off[k + 1]], r[off[k]:off[k + 1]]) < L1_TOL
+
+
+def test_batch_host_entry_point(spl):
+    px = W.array_pixels(50, seed=15, n_bins=700)
+    d, off, _ = spl.batch_stationary(px)
+    h, off2, reps = spl.batch_stationary_host(px)
+    np.testing.assert_array_equal(off, off2)
+    np.testing.assert_array_equal(h, d.cpu().numpy())
+
+
+def test_batch_lambda2_estimates(spl):
+    """The |lambda_2| and phase the stop rule estimates track LAPACK's
+    eigenvalues of P~ (Sec. 4) for pixels whose subdominant mode is separated."""
+    px = W.array_pixels(16, seed=16, n_bins=300)
+    _, _, reps = spl.batch_stationary(px)
+    good = 0
+    for k, p in enumerate(W.as_dicts(px)):
+        Pt = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+        w = np.linalg.eigvals(Pt)
+        w = w[np.argsort(-np.abs(w))]
+        if abs(abs(w[1]) - abs(w[3])) > 0.05 and abs(w[1]) > 0.05:
+            good += 1
+            assert abs(reps["lambda2_abs"][k] - abs(w[1])) < 0.1 * abs(w[1]) + 0.02
+    assert good >= 1
+
+
+def test_batch_invalid_pixel_rejected(spl):
+    px = W.array_pixels(4, seed=17, n_bins=100)
+    px["sigma"][2] = -1.0
+    with pytest.raises(spl.SplError) as ei:
+        spl.batch_stationary(px)
+    assert ei.value.status == spl.SPL_EINVAL
+
+
+def test_batch_empty(spl):
+    px = W.array_pixels(0, seed=1)
+    out, off, reps = spl.batch_stationary(px, out=torch.empty(1, device="cuda"))
+    assert len(reps) == 0
