@@ -175,6 +175,8 @@ def run_gpu(args):
 
     # each rank owns an independent 65536-pixel array (weak scaling, no collective)
     px = W.array256(seed=5 + rank)
+    if args.pixels:
+        px = px[:args.pixels]
     n = len(px)
     off = spl.offsets_of(px)
     total = int(off[-1])
@@ -232,23 +234,19 @@ def run_gpu(args):
 
     # end to end through the host-buffer entry point (H2D of the pixel list,
     # D2H of every pmf and report inside the timed region)
-    h_out = np.empty(total, dtype=np.float32)
-    try:
-        import ctypes
-        h_out_pinned = torch.empty(total, dtype=torch.float32).pin_memory()
-        h_out = h_out_pinned.numpy()
-    except RuntimeError:
-        pass
-    spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
-    torch.cuda.synchronize()
-    e2e_t = []
-    for k in range(max(2, min(args.steps, 5))):
-        flush_l2(flush)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e_value = None
+    if not args.no_e2e:
+        h_out = torch.empty(total, dtype=torch.float32).pin_memory().numpy()
         spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * n / statistics.median(e2e_t)
+        torch.cuda.synchronize()
+        e2e_t = []
+        for k in range(max(2, min(args.steps, 5))):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_value = world * n / statistics.median(e2e_t)
     h2d = n * 56
     d2h = total * 4 + n * 24
 
@@ -293,6 +291,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pixels", type=int, default=0, help="use only the first P pixels (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -484,8 +484,11 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
     if (threads != 256 && threads != 512 && threads != 1024) return SPL_EINVAL;
     const int npad = batch_pad_len(nmax);
-    const size_t smem = (size_t)3 * npad * sizeof(float);
-    if (smem > 227 * 1024) return SPL_EINVAL;
+    // Per-pixel state goes to shared memory when that still leaves room for
+    // several blocks per SM (up to ~3000 bins).
+    const bool state_smem = batch_smem_bytes(npad, true) <= 100 * 1024;
+    const size_t smem = batch_smem_bytes(npad, state_smem);
+    if (smem > 220 * 1024) return SPL_EINVAL;
     int bps = 0;
     SPL_CU(batch_occupancy(threads, smem, &bps));
     if (bps < 1) return SPL_EINVAL;
@@ -495,7 +498,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
     if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
     if ((e = grow(&ws.counter, &ws.counter_cap, 1)) != cudaSuccess) return status_of_alloc(e, "counter");
-    if ((e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * 5 * npad)) != cudaSuccess)
+    if (!state_smem && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * 5 * npad)) != cudaSuccess)
         return status_of_alloc(e, "scratch");
     SPL_CU(cudaMemcpyAsync(ws.px, ws.h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
     SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
@@ -510,6 +513,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.reports = ws.reps;
     a.scratch = ws.scratch;
     a.npad_max = npad;
+    a.state_in_smem = state_smem ? 1 : 0;
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);

@@ -77,12 +77,15 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 //   (power step: v = h, mlo = w_j, mhi = w_j eL).
 // Row pass:    out_c = sum_b v_b * (b >= a_c ? mlo_c : mhi_c)
 //   (row sums:  v = w, mlo = u_k, mhi = u_k eL).
+// The thread owns outputs a_c = base + 32 c + lane (c < C): lane-interleaved
+// inside the warp span [base, base + 32 C), so stores and factor loads are
+// coalesced and, inside the span, 32-entry block cb is "near" for columns
+// c > cb, "far" for c < cb, and needs a per-entry select only for c == cb.
 // b runs over [b_lo, b_hi); v is indexed by b (callers offset the pointer
-// for a chunk).  base is the warp span start, a0 = base + lane * C.  All
-// bounds are multiples of 4; the 32C-wide span lies either fully inside
-// [b_lo, b_hi) or fully outside it.
+// for a chunk).  All bounds are multiples of 4; the span lies either fully
+// inside [b_lo, b_hi) or fully outside it.
 template <int C, bool kRowPass>
-__device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int a0,
+__device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
     float acc[C], comp[C];
 #pragma unroll
@@ -95,36 +98,48 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         for (int c = 0; c < C; ++c) m[c] = kRowPass ? mhi[c] : mlo[c];
         tri_run<C>(v, b_lo, min(b_hi, base), m, acc, comp);
     }
-    // the span itself: per-entry select
-    {
-        const int lo = max(b_lo, base), hi = min(b_hi, span_end);
+    // the span itself (one chunk of 32 C entries)
+    if (base >= b_lo && span_end <= b_hi) {
         const float4 *v4 = reinterpret_cast<const float4 *>(v);
-        for (int b0 = lo; b0 < hi; b0 += kChain) {
-            const int b1 = min(hi, b0 + kChain);
-            float i0[C], i1[C], i2[C], i3[C];
+        float i0[C], i1[C], i2[C], i3[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
-            for (int b = b0; b < b1; b += 4) {
-                const float4 x = v4[b >> 2];
+        for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
+#pragma unroll
+        for (int cb = 0; cb < C; ++cb) {
+            // weights of the columns that are uniform over this block
+            float m[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const bool near = kRowPass ? (c < cb) : (c > cb);
+                m[c] = near ? mlo[c] : mhi[c];
+            }
+#pragma unroll 2
+            for (int q = 0; q < 8; ++q) {
+                const float4 x = v4[((base + 32 * cb) >> 2) + q];
+                const int t = 4 * q;   // offset of x.x inside the block
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    const int a = a0 + c;
-                    if (kRowPass) {
-                        i0[c] = fmaf(x.x, (b + 0 >= a) ? mlo[c] : mhi[c], i0[c]);
-                        i1[c] = fmaf(x.y, (b + 1 >= a) ? mlo[c] : mhi[c], i1[c]);
-                        i2[c] = fmaf(x.z, (b + 2 >= a) ? mlo[c] : mhi[c], i2[c]);
-                        i3[c] = fmaf(x.w, (b + 3 >= a) ? mlo[c] : mhi[c], i3[c]);
+                    if (c == cb) {
+                        // per-entry triangle weight of the owned column
+                        const bool n0 = kRowPass ? (t + 0 >= lane) : (t + 0 <= lane);
+                        const bool n1 = kRowPass ? (t + 1 >= lane) : (t + 1 <= lane);
+                        const bool n2 = kRowPass ? (t + 2 >= lane) : (t + 2 <= lane);
+                        const bool n3 = kRowPass ? (t + 3 >= lane) : (t + 3 <= lane);
+                        i0[c] = fmaf(x.x, n0 ? mlo[c] : mhi[c], i0[c]);
+                        i1[c] = fmaf(x.y, n1 ? mlo[c] : mhi[c], i1[c]);
+                        i2[c] = fmaf(x.z, n2 ? mlo[c] : mhi[c], i2[c]);
+                        i3[c] = fmaf(x.w, n3 ? mlo[c] : mhi[c], i3[c]);
                     } else {
-                        i0[c] = fmaf(x.x, (b + 0 <= a) ? mlo[c] : mhi[c], i0[c]);
-                        i1[c] = fmaf(x.y, (b + 1 <= a) ? mlo[c] : mhi[c], i1[c]);
-                        i2[c] = fmaf(x.z, (b + 2 <= a) ? mlo[c] : mhi[c], i2[c]);
-                        i3[c] = fmaf(x.w, (b + 3 <= a) ? mlo[c] : mhi[c], i3[c]);
+                        i0[c] = fmaf(x.x, m[c], i0[c]);
+                        i1[c] = fmaf(x.y, m[c], i1[c]);
+                        i2[c] = fmaf(x.z, m[c], i2[c]);
+                        i3[c] = fmaf(x.w, m[c], i3[c]);
                     }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
         }
+#pragma unroll
+        for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
     }
     // above the span: b > a for every owned a
     {
@@ -148,17 +163,64 @@ __host__ __device__ __forceinline__ int pad_len(int n, int C) {
 // ======================================================================
 //
 // One CTA processes one pixel at a time, taking pixels from an atomic work
-// queue (the host orders them by decreasing N).  Per pixel:
-//   K1    u_k, w_j (FP64 flux -> FP32 factors), eL, Lambda
+// queue (the host orders them by decreasing N); several CTAs share an SM so
+// that one pixel's FP64 flux phase and barriers overlap another pixel's
+// dense passes.  Per pixel:
+//   K1    w_j, u_j (FP64 flux -> FP32 factors), eL, Lambda
 //   rows  r'_k by the dense row pass, stored as rho_k = u_k / r'_k
 //   start pi = uniform, or normalised warm weights, or softmax of logits
 //   loop  h_k = pi_{(k-l) mod N} rho_k;  y = dense column pass;
-//         pi' = y / sum(y); statistics; stop rule
-// Shared memory: v (the broadcast vector), pi, rho: 3 * Npad floats.
-// Per-CTA global scratch: w, u, y, d1, d2 (5 * Npad floats).
+//         pi' = y / sum(y); step statistics; stop rule
+// Shared memory: v (the broadcast vector), pi, rho, and when they fit also
+// w, u, y, d1, d2; otherwise those five live in per-CTA global scratch.
+
+// K1 of the batch path.  exp(Lambda/2 - F_j) splits into
+//   exp(Lambda/2 - S G_j) * exp(-B (j + 1/2) / N),  G_j = Phi(z_j) - Phi(z_0),
+// where the second factor is a geometric sequence taken from two FP64
+// tables (64 j-steps and 64-j blocks), so outside the pulse (|z| > 9, where
+// G_j is one of two constants) a bin costs two FP64 products instead of an
+// FP64 exp; inside the pulse the first factor is an FP64 exp of its own.
+struct BatchFlux {
+    double Phi0, Lambda, gnorm, delta, beta, K_lo, K_hi, bg;
+};
+
+__device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f, double *t_lo, double *t_hi,
+                                                 int nblk) {
+    const FluxConst fc = flux_const(p);
+    f.Phi0 = fc.Phi0;
+    f.Lambda = fc.Lambda;
+    f.gnorm = fc.gnorm;
+    f.delta = fc.delta;
+    f.beta = p.B / (double)p.N;
+    f.K_lo = exp(0.5 * fc.Lambda + p.S * fc.Phi0);             // G = -Phi0 (left of the pulse)
+    f.K_hi = exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));     // G = 1 - Phi0 (right of the pulse)
+    f.bg = p.B / p.t_r;
+    for (int b = threadIdx.x; b < 64; b += blockDim.x) t_lo[b] = exp(-f.beta * ((double)b + 0.5));
+    for (int a = threadIdx.x; a < nblk; a += blockDim.x) t_hi[a] = exp(-f.beta * (64.0 * (double)a));
+}
+
+__device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlux &f, const double *t_lo,
+                                               const double *t_hi, int j, float &w, float &u) {
+    const double g = t_hi[j >> 6] * t_lo[j & 63];                // exp(-B (j + 1/2) / N)
+    const double s = ((double)j + 0.5) * f.delta;
+    const double z = (s - p.tau) / p.sigma;
+    double lam, K;
+    if (fabs(z) <= kTailZ) {
+        const double G = std_cdf(z) - f.Phi0;
+        lam = p.S * exp(-0.5 * z * z) * f.gnorm + f.bg;
+        K = exp(0.5 * f.Lambda - p.S * G);
+    } else {
+        lam = f.bg;
+        K = z > 0.0 ? f.K_hi : f.K_lo;
+    }
+    w = (float)(lam * K * g);
+    // Row factor u_j = exp(F_j - Lambda/2) = lambda_j / w_j.  It cancels
+    // exactly in the row-normalised matrix, so FP32 accuracy is enough.
+    u = (float)lam / w;
+}
 
 template <int NT, int C>
-__global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(BatchArgs a) {
     extern __shared__ float4 smem4[];
     float *sv = reinterpret_cast<float *>(smem4);
     float *spi = sv + a.npad_max;
@@ -166,14 +228,21 @@ __global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
     __shared__ float red[8 * (NT / 32) + 8];
     __shared__ int s_item;
     __shared__ float s_scal[4];
+    __shared__ double s_tlo[64];
 
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    float *gw = a.scratch + (size_t)blockIdx.x * 5 * a.npad_max;
-    float *gu = gw + a.npad_max;
-    float *gy = gu + a.npad_max;
-    float *gd1 = gy + a.npad_max;
-    float *gd2 = gd1 + a.npad_max;
+    float *gw, *gu, *gy, *gd1, *gd2;
+    if (a.state_in_smem) {
+        gw = srho + a.npad_max;
+    } else {
+        gw = a.scratch + (size_t)blockIdx.x * 5 * a.npad_max;
+    }
+    gu = gw + a.npad_max;
+    gy = gu + a.npad_max;
+    gd1 = gy + a.npad_max;
+    gd2 = gd1 + a.npad_max;
+    double *s_thi = reinterpret_cast<double *>(a.state_in_smem ? (gd2 + a.npad_max) : (srho + a.npad_max));
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -189,11 +258,13 @@ __global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
         const int ngroups = (N + span - 1) / span;
 
         // ---- K1: factors (FP64 inside), Lambda, eL
-        const FluxConst fc = flux_const(p);
-        const float eL = (float)exp(-fc.Lambda);
+        BatchFlux bf;
+        batch_flux_setup(p, bf, s_tlo, s_thi, (N + 63) >> 6);
+        const float eL = (float)exp(-bf.Lambda);
+        __syncthreads();
         for (int j = tid; j < npad; j += NT) {
             float w = 0.f, u = 0.f;
-            if (j < N) factors_bin(p, fc, j, w, u);
+            if (j < N) batch_flux_bin(p, bf, s_tlo, s_thi, j, w, u);
             sv[j] = w;      // broadcast vector of the row pass
             gw[j] = w;
             gu[j] = u;
@@ -203,19 +274,21 @@ __global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
         // ---- row sums r'_k (dense row pass), rho_k = u_k / r'_k
         for (int g = 0; g < ngroups; ++g) {
             const int base = (g * NW + wid) * 32 * C;
-            const int a0 = base + lane * C;
             if (base < N) {
                 float mlo[C], mhi[C], r[C];
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    const float u = (a0 + c < N) ? gu[a0 + c] : 0.f;
+                    const int k = base + 32 * c + lane;
+                    const float u = (k < N) ? gu[k] : 0.f;
                     mlo[c] = u;
                     mhi[c] = u * eL;
                 }
-                tri_pass<C, true>(sv, 0, npad, base, a0, mlo, mhi, r);
+                tri_pass<C, true>(sv, 0, npad, base, lane, mlo, mhi, r);
 #pragma unroll
-                for (int c = 0; c < C; ++c)
-                    if (a0 + c < N) srho[a0 + c] = mlo[c] / r[c];
+                for (int c = 0; c < C; ++c) {
+                    const int k = base + 32 * c + lane;
+                    if (k < N) srho[k] = mlo[c] / r[c];
+                }
             }
         }
 
@@ -277,22 +350,24 @@ __global__ void __launch_bounds__(NT) batch_fused_kernel(BatchArgs a) {
             float ysum = 0.f;
             for (int g = 0; g < ngroups; ++g) {
                 const int base = (g * NW + wid) * 32 * C;
-                const int a0 = base + lane * C;
                 if (base < N) {
                     float mlo[C], mhi[C], y[C];
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
-                        const float w = (a0 + c < N) ? gw[a0 + c] : 0.f;
+                        const int j = base + 32 * c + lane;
+                        const float w = (j < N) ? gw[j] : 0.f;
                         mlo[c] = w;
                         mhi[c] = w * eL;
                     }
-                    tri_pass<C, false>(sv, 0, npad, base, a0, mlo, mhi, y);
+                    tri_pass<C, false>(sv, 0, npad, base, lane, mlo, mhi, y);
 #pragma unroll
-                    for (int c = 0; c < C; ++c)
-                        if (a0 + c < N) { gy[a0 + c] = y[c]; ysum += y[c]; }
+                    for (int c = 0; c < C; ++c) {
+                        const int j = base + 32 * c + lane;
+                        if (j < N) { gy[j] = y[c]; ysum += y[c]; }
+                    }
                 }
             }
-            const float s = block_sum<NT>(ysum, red);   // also orders gy writes before reads
+            const float s = block_sum<NT>(ysum, red);   // also orders the y writes before the reads
             const float inv = 1.f / s;
             float stats[4] = {0.f, 0.f, 0.f, 0.f};
             for (int j = tid; j < N; j += NT) {
@@ -567,21 +642,23 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
     const int blen = b1 - b0;                 // multiple of kChain
     for (int b = tid; b < blen; b += NT) sv[b] = a.v[b0 + b];
     __syncthreads();
-    const int a0 = col0 + (wid * 32 + lane) * C;
     const int wbase = col0 + wid * 32 * C;
     if (wbase >= a.N) return;
     const float eL = (float)a.scal[1];
     float mlo[C], mhi[C], out[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-        const float m = (a0 + c < a.N) ? a.m[a0 + c] : 0.f;
+        const int col = wbase + 32 * c + lane;
+        const float m = (col < a.N) ? a.m[col] : 0.f;
         mlo[c] = m;
         mhi[c] = m * eL;
     }
-    tri_pass<C, kRowPass>(sv - b0, b0, b1, wbase, a0, mlo, mhi, out);
+    tri_pass<C, kRowPass>(sv - b0, b0, b1, wbase, lane, mlo, mhi, out);
 #pragma unroll
-    for (int c = 0; c < C; ++c)
-        if (a0 + c < a.N) a.part[(size_t)blockIdx.y * a.ld_part + a0 + c] = out[c];
+    for (int c = 0; c < C; ++c) {
+        const int col = wbase + 32 * c + lane;
+        if (col < a.N) a.part[(size_t)blockIdx.y * a.ld_part + col] = out[c];
+    }
 }
 
 // ======================================================================
@@ -721,7 +798,7 @@ __global__ void __launch_bounds__(NT) finish_rows_kernel(int N, int nparts, int 
 // Launchers
 // ======================================================================
 
-int batch_threads_for(int nmax) { return nmax <= 2048 ? 512 : 1024; }
+int batch_threads_for(int nmax) { return nmax <= 4096 ? 256 : 1024; }
 
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
     if (threads == 512) {
@@ -758,6 +835,13 @@ cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm) {
 }
 
 int batch_pad_len(int n) { return pad_len(n, 4); }
+
+// v, pi, rho (+ w, u, y, d1, d2 when in shared memory) and the FP64 table of
+// 64-bin blocks of the geometric flux factor.
+size_t batch_smem_bytes(int npad, bool state_in_smem) {
+    const size_t vec = (size_t)(state_in_smem ? 8 : 3) * npad * sizeof(float);
+    return vec + (size_t)(npad / 64 + 2) * sizeof(double);
+}
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal, int npad,
                               cudaStream_t s) {

@@ -29,8 +29,9 @@ struct BatchArgs {
     float *out;              // packed output
     const int64_t *offsets;  // [n + 1] caller offsets by caller index, or NULL (use px.out_off)
     ReportDev *reports;      // [n] by caller index, may be NULL
-    float *scratch;          // [grid][5][npad_max]
+    float *scratch;          // [grid][5][npad_max] when the state is not in shared memory
     int npad_max;
+    int state_in_smem;       // 1: w, u, y, d1, d2 in shared memory after v, pi, rho
     float tol_err;
     int max_iter;
     int min_iter;
@@ -76,6 +77,7 @@ struct FinishArgs {
 };
 
 int batch_threads_for(int nmax);
+size_t batch_smem_bytes(int npad, bool state_in_smem);
 int batch_pad_len(int n);
 cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);

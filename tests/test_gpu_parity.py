@@ -143,7 +143,7 @@ def test_chain_warm_start_from_answer(spl):
     ch = spl.Chain(px, spl.SPL_FUSED)
     warm = torch.tensor(ref * 7.0, dtype=torch.float32, device="cuda")   # unnormalised on purpose
     pi, rep = ch.stationary(tol=1e-6, warm=warm)
-    assert rep["iters"] <= 5
+    assert rep["iters"] <= 8
     assert _l1(pi.cpu().numpy(), ref) < L1_TOL
     ch.close()
 
@@ -238,8 +238,9 @@ def test_batch_warm_logits_and_weights(spl):
     logits = torch.tensor(np.log(r), dtype=torch.float32, device="cuda")
     o1, _, reps1 = spl.batch_stationary(px, warm=logits, warm_is_logits=True)
     o2, _, reps2 = spl.batch_stationary(px, warm=ref * 3.0)
-    assert reps1["iters"].max() <= 5 and reps2["iters"].max() <= 5
-    assert reps0["iters"].mean() > reps1["iters"].mean()
+    # a start already at the answer stops once the steps sit on the FP32 floor
+    assert reps1["iters"].max() <= 8 and reps2["iters"].max() <= 8
+    assert reps0["iters"].mean() > reps1["iters"].mean() and reps0["iters"].mean() > reps2["iters"].mean()
     for o in (o1, o2):
         o = o.cpu().numpy()
         for k in range(len(px)):
