@@ -160,6 +160,34 @@ SPL_API spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int3
                                        const float *h_warm, float *h_out, spl_report_t *h_reports,
                                        void *stream);
 
+/*
+ * spl_batch_stationary without any allocation.  The paper has no counterpart;
+ * this entry point exists for callers that may not allocate device memory:
+ * real-time pipelines that ban allocation once running (cudaMalloc can
+ * synchronise the device and its latency is unbounded) and plug-ins inside
+ * an application whose own allocator owns the GPU memory budget.
+ *   Arguments are those of spl_batch_stationary (d_warm: NULL or packed
+ *   nonnegative weights; d_out and d_offsets caller-owned device arrays;
+ *   h_reports NULL or host [n]).
+ *   The kernel's device scratch (work list, queue counter, reports) is a
+ *   fixed file-scope device array of about 4 MB that every GPU loading the
+ *   library holds until the process exits; host staging is static too.  No
+ *   cudaMalloc, cudaFree or other allocating routine is called.
+ *   Limits: n <= 65536 pixels and 2 <= n_bins <= 3072 per pixel; larger
+ *   requests return SPL_EINVAL before any device work.
+ *   The first call on a device looks up the array's device address for that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  All calls share the array and it keeps the previous call's
+ *   contents (the queue counter is cleared by each call); calls whose work
+ *   overlaps on the GPU race on it, so issue them one after the other.
+ *   With h_reports the call synchronises `stream`; without, it is
+ *   asynchronous.  Returns the worst per-pixel status, as the batch call.
+ */
+SPL_API spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels, int32_t n, double tol,
+                                                  int32_t max_iter, const float *d_warm, float *d_out,
+                                                  const int64_t *d_offsets, spl_report_t *h_reports,
+                                                  void *stream);
+
 /* Materialised chains only: copy P (the paper's unnormalised P of Eq. 4/6,
  * lambda_j E_ij without the constant 1/(1 - e^-Lambda)) to d_P, row-major
  * [n_bins][n_bins].  SPL_EINVAL for fused chains. */

@@ -46,7 +46,7 @@ REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_
 
 # Symbols include/spl.h declares (checked by the CPU tests).
 EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_stationary_ex", "spl_batch_kernel_ms",
-            "spl_batch_stationary_host", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
+            "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version"]
 
 _lib = None
@@ -86,6 +86,9 @@ def lib():
         L.spl_batch_stationary_host.argtypes = [ctypes.POINTER(spl_pixel_t), i32, f64, i32, vp, vp,
                                                 ctypes.POINTER(spl_report_t), vp]
         L.spl_batch_stationary_host.restype = ctypes.c_int
+        L.spl_batch_stationary_noalloc.argtypes = [ctypes.POINTER(spl_pixel_t), i32, f64, i32, vp, vp, vp,
+                                                   ctypes.POINTER(spl_report_t), vp]
+        L.spl_batch_stationary_noalloc.restype = ctypes.c_int
         L.spl_batch_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
         L.spl_batch_kernel_ms.restype = ctypes.c_int
         L.spl_matrix.argtypes = [vp, vp]
@@ -212,6 +215,28 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
+    return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
+                             offsets=None, reports: bool = True, stream=None):
+    """spl_batch_stationary_noalloc: the batch solver for callers that may not
+    allocate device memory (its scratch is a fixed device array inside the
+    library).  ``out`` and ``offsets`` are caller-owned device tensors; they
+    are created here only when not given.  Returns (out, offsets, reports)."""
+    import torch
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    n = len(px)
+    off = offsets_of(px)
+    if offsets is None:
+        offsets = torch.from_numpy(off).to("cuda")
+    if out is None:
+        out = torch.empty(max(1, int(off[-1])), dtype=torch.float32, device="cuda")
+    arr = pixels_to_c(px)
+    reps = (spl_report_t * max(1, n))() if reports else None
+    st = lib().spl_batch_stationary_noalloc(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out),
+                                            _dptr(offsets), reps, _stream_ptr(stream))
+    _check(st, "spl_batch_stationary_noalloc", (SPL_OK, SPL_ENOCONV))
     return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
 
 
