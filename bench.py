@@ -1,11 +1,14 @@
 """Benchmark: stationary pmfs per second at N = 2000 bins, each within 1e-6 L1
-of the FP64 oracle.
+of the FP64 oracle, learned + batched against plain batched.
 
 Workload (one step): the 256 x 256 pixel array (65536 pixels, N = 2000,
 t_r = 100 ns, t_d = 75 ns, tau ~ U[5,95] ns, sigma ~ U[0.2,1] ns,
 S, B ~ logU[0.01,5], seed 5).  A step runs the whole path through the C ABI:
-dead-time shift (host), FP64 cumulative flux, row sums and matrix-free power
-iteration of every pixel to the 1e-6 stop rule, in one persistent launch.
+the warm-start network's forward pass on the tensor cores, the dead-time
+shift (host), FP64 cumulative flux, row sums and matrix-free power iteration
+of every pixel to the 1e-6 stop rule in one persistent launch.  The network
+is trained first (untimed) on 200k pmfs the plain solver produces.  The plain
+arm (uniform start) is timed on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -161,6 +164,23 @@ def flush_l2(buf):
     buf.add_(1.0)       # writes 256 MiB (> 129 MB L2)
 
 
+def timed_steps(step_fn, steps, flush, stream, kernel_ms_fn=None):
+    """Per-step device times (CUDA events on the launching stream, L2 flushed
+    between steps outside the events) and, if given, the batch kernel time."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kern = []
+    for k in range(steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        step_fn()
+        ev[k][1].record(stream)
+        if kernel_ms_fn is not None:
+            kern.append(kernel_ms_fn())
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], kern
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -169,9 +189,10 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2509_20500_gb300 import build, spl, workloads as W
+    from paper_2509_20500_gb300 import build, spl, train as T, workloads as W
     build.build()
-    L = spl.lib()
+    spl.lib()
+    peaks = measured_peaks() or {}
 
     # each rank owns an independent 65536-pixel array (weak scaling, no collective)
     px = W.array256(seed=5 + rank)
@@ -186,36 +207,55 @@ def run_gpu(args):
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(time_kernel=False, reports=False):
+    def plain_step(time_kernel=False, reports=False):
         return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
                                     c_pixels=c_px, time_kernel=time_kernel)
 
-    # untimed: per-pixel iteration counts for the algorithmic work (deterministic)
-    _, _, reps = step(reports=True)
-    assert np.all(reps["status"] == 0), "some pixels did not converge"
+    # ---- plain batched arm (uniform start)
+    _, _, reps_plain = plain_step(reports=True)
+    assert np.all(reps_plain["status"] == 0), "some pixels did not converge"
     for _ in range(args.warmup):
-        step()
+        plain_step()
     torch.cuda.synchronize()
+    plain_ms_list, plain_kern = timed_steps(lambda: plain_step(time_kernel=True), args.steps, flush, stream,
+                                            spl.batch_kernel_ms)
+    plain_ms = sum(plain_ms_list) / len(plain_ms_list)
 
+    # ---- learned warm start: trained (untimed) on pmfs the method generates
+    learned = not args.no_learned
+    if learned:
+        t0 = time.perf_counter()
+        tpx, ttg = T.make_training_set(args.train_pixels, seed=2)
+        net = T.train(tpx, ttg, epochs=args.epochs, batch=4096, lr=3e-3)
+        del ttg
+        train_s = time.perf_counter() - t0
+
+        def learned_step(reports=False):
+            return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
+                                        c_pixels=c_px)
+
+        _, _, reps_l = learned_step(reports=True)
+        assert np.all(reps_l["status"] == 0), "some pixels did not converge (learned start)"
+        for _ in range(args.warmup):
+            learned_step()
+        torch.cuda.synchronize()
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kern_ms = []
-    for k in range(args.steps):
-        flush_l2(flush)
-        ev[k][0].record(stream)
-        step(time_kernel=True)
-        ev[k][1].record(stream)
-        kern_ms.append(spl.batch_kernel_ms())
+    if learned:
+        step_ms, kern_ms = timed_steps(lambda: learned_step(), args.steps, flush, stream, spl.batch_kernel_ms)
+        reps = reps_l
+    else:
+        step_ms, kern_ms = timed_steps(lambda: plain_step(time_kernel=True), args.steps, flush, stream,
+                                       spl.batch_kernel_ms)
+        reps = reps_plain
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -231,44 +271,102 @@ def run_gpu(args):
     kms = statistics.median(kern_ms)
     achieved = flop / (kms / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "batch_fused_kernel", "kernel_ms": kms,
+            "work": "2 FLOP x N^2 x (1 + iters) per pixel (row pass + power steps, one FFMA per entry)",
+            "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock), derived"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
 
-    # end to end through the host-buffer entry point (H2D of the pixel list,
-    # D2H of every pmf and report inside the timed region)
+    extra = {}
+    if learned:
+        # tensor-core roofline of the network's forward pass over the array
+        chunks = [(i, min(n, i + 4096)) for i in range(0, n, 4096)]
+        lg = torch.empty((4096, 2048), dtype=torch.float32, device=dev)
+        for a, b in chunks[:2]:
+            net.forward(px[a:b], out=lg[:b - a])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for a, b in chunks:
+            net.forward(px[a:b], out=lg[:b - a])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mlp_ms = e0.elapsed_time(e1)
+        mlp_flop = 2.0 * n * (5 * 512 + 3 * 512 * 512 + 512 * 2000)
+        tpeak = float(peaks.get("bf16_tflops", 1900.0))
+        extra["learned"] = {"value": value, "ms_per_step": ms, "iters_mean": float(reps_l["iters"].mean()),
+                            "iters_max": int(reps_l["iters"].max()), "train_seconds": train_s,
+                            "train_pixels": args.train_pixels, "epochs": args.epochs,
+                            "mlp_roofline": {"bound": "tensor", "achieved": mlp_flop / (mlp_ms / 1e3) / 1e12,
+                                             "peak": tpeak, "unit": "TFLOP/s",
+                                             "frac": mlp_flop / (mlp_ms / 1e3) / 1e12 / tpeak,
+                                             "ms": mlp_ms, "peak_basis": "MEASURED_PEAKS bf16_tflops (burst), of measured"}}
+    extra["plain"] = {"value": world * n / (plain_ms / 1e3), "ms_per_step": plain_ms,
+                      "iters_mean": float(reps_plain["iters"].mean()), "iters_max": int(reps_plain["iters"].max()),
+                      "kernel_ms": statistics.median(plain_kern)}
+
+    # materialised vs matrix-free power step on one N = 10000 pixel (400 MB P)
+    if not args.no_highres and rank == 0:
+        hp = W.pixel(10000, 75.0, 30.0, 0.3, 0.5, 0.5)
+        hr = {}
+        ch = spl.Chain(hp, spl.SPL_MATERIALIZED)
+        gemv_ms = ch.time_pass(20)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        gbs = 4.0 * 1e8 / (gemv_ms / 1e3) / 1e9
+        hr["materialized_gemv"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                   "ms_per_pass": gemv_ms, "bytes": 4e8,
+                                   "peak_basis": "MEASURED_PEAKS hbm_gbs, of measured"}
+        _, rep = ch.stationary(tol=TOL)
+        hr["materialized_iters"] = int(rep["iters"])
+        ch.close()
+        ch = spl.Chain(hp, spl.SPL_FUSED)
+        fused_ms = ch.time_pass(20)
+        tf = 2.0 * 1e8 / (fused_ms / 1e3) / 1e12
+        hr["fused_pass"] = {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                            "ms_per_pass": fused_ms}
+        ch.close()
+        extra["highres_n10000"] = hr
+
+    # end to end through the public API: pixel list from host memory (copied
+    # inside the call), every pmf read back to pinned host memory, per step
     e2e_value = None
     if not args.no_e2e:
-        h_out = torch.empty(total, dtype=torch.float32).pin_memory().numpy()
-        spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
+        h_out = torch.empty(total, dtype=torch.float32).pin_memory()
+        fn = (lambda: learned_step()) if learned else (lambda: plain_step())
+        fn()
+        h_out.copy_(out)
         torch.cuda.synchronize()
         e2e_t = []
         for k in range(max(2, min(args.steps, 5))):
             flush_l2(flush)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out)
+            fn()
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
             e2e_t.append(time.perf_counter() - t0)
         e2e_value = world * n / statistics.median(e2e_t)
     h2d = n * 56
-    d2h = total * 4 + n * 24
+    d2h = total * 4
 
+    launches = 1 + (6 * ((n + 4095) // 4096) if learned else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pixels_per_gpu": n, "n_bins": 2000, "tol_l1": TOL,
-                   "path": "plain batched (uniform start), matrix-free dense power step",
+                   "path": ("learned warm start (tcgen05 MLP) + batched matrix-free power iteration" if learned
+                            else "plain batched (uniform start), matrix-free dense power step"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}, pixels sharded, no collective"},
         "iters": {"mean": float(reps["iters"].mean()), "max": int(reps["iters"].max())},
-        "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "batch_fused_kernel", "kernel_ms": kms,
-                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock)"},
+        "gpu_launches": launches * args.steps,
+        "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
     }
-    if clocks.get("sm_mhz"):
-        line["roofline"]["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, _ = cpu_sample(px, args.cpu_sample)
         rate, dt, used = oracle_rate(sample, os.cpu_count() or 1)
@@ -293,6 +391,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pixels", type=int, default=0, help="use only the first P pixels (profiling)")
+    ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
+    ap.add_argument("--no-highres", action="store_true")
+    ap.add_argument("--train-pixels", type=int, default=200_000)
+    ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -131,9 +131,18 @@ SPL_API spl_status_t spl_batch_stationary(const spl_pixel_t *h_pixels, int32_t n
                                   const float *d_warm, float *d_out, const int64_t *d_offsets,
                                   spl_report_t *h_reports, void *stream);
 
+/* Kinds of warm start for spl_batch_stationary_ex (d_warm). */
+typedef enum {
+    SPL_WARM_WEIGHTS = 0,   /* nonnegative weights packed like d_out; start = weights / sum */
+    SPL_WARM_LOGITS = 1,    /* logits packed like d_out; start = softmax */
+    SPL_WARM_LEARNED = 2,   /* rows of warm_ld floats per pixel (caller order) in the learned frame:
+                               start_j ~ exp(z[(j - c) mod N] + log lambda(s_j)), c = floor(tau / Delta) */
+} spl_warm_kind_t;
+
 /* Options for spl_batch_stationary_ex. */
 typedef struct {
-    int32_t warm_is_logits;   /* 1: d_warm holds logits, the start is their softmax per pixel */
+    int32_t warm_kind;        /* spl_warm_kind_t, used when d_warm != NULL */
+    int32_t warm_ld;          /* row stride of SPL_WARM_LEARNED logits (>= n_bins) */
     int32_t min_iter;         /* steps always taken before the stop rule may fire (>= 1) */
     int32_t threads;          /* threads per block, 0 = library default */
     int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
@@ -188,10 +197,61 @@ SPL_API spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels, i
                                                   const int64_t *d_offsets, spl_report_t *h_reports,
                                                   void *stream);
 
+/*
+ * Learned warm start (the paper has no network; this follows its batched use
+ * case).  A 5 -> 4 x 512 (GELU) -> 2000 MLP, BF16 weights with FP32
+ * accumulation on the tensor cores, maps (sub-bin pulse position, sigma,
+ * log S, log B, x_d / t_r) of an n_bins = 2000 pixel to a log-correction of
+ * the flux prior lambda(s_j) in a frame rolled to the pulse bin; its softmax
+ * starts the power iteration, which always runs to the stop rule (the plain
+ * iteration is the judge of the network's error).
+ *   spl_mlp_create   : device network for batches of up to max_batch pixels,
+ *                      seeded uniform fan-in initialisation; owns its scratch.
+ *   spl_mlp_param_count / set_params / get_params : packed FP32 parameters,
+ *                      per layer W (rows x cols, row-major) then b.
+ *   spl_mlp_forward  : logits [n][2048] of pixels with n_bins == 2000 (B > 0);
+ *                      d_logits may be NULL (kept inside the network).
+ *   spl_mlp_loss_grad: mean cross-entropy of the start vector against d_target
+ *                      ([n][2000] pmfs on the device) and, into h_grads
+ *                      (packed like the parameters, may be NULL), its gradient.
+ *   spl_mlp_train_step: one AdamW step on that loss (lr, weight_decay).
+ *   spl_batch_stationary_learned: forward pass, then spl_batch_stationary
+ *                      started from the network's warm start; stream must be
+ *                      the network's stream.
+ * All run on the network's stream; errors as the other calls.
+ */
+typedef struct spl_mlp spl_mlp_t;
+SPL_API spl_status_t spl_mlp_create(int32_t max_batch, uint64_t seed, void *stream, spl_mlp_t **out);
+SPL_API int64_t spl_mlp_param_count(void);
+SPL_API spl_status_t spl_mlp_set_params(spl_mlp_t *m, const float *h_params, int64_t count);
+SPL_API spl_status_t spl_mlp_get_params(spl_mlp_t *m, float *h_params, int64_t count);
+SPL_API spl_status_t spl_mlp_forward(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, float *d_logits);
+SPL_API spl_status_t spl_mlp_loss_grad(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, const float *d_target,
+                                       float *h_loss, float *h_grads);
+SPL_API spl_status_t spl_mlp_train_step(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, const float *d_target,
+                                        float lr, float weight_decay, float *h_loss);
+SPL_API const float *spl_mlp_logits(spl_mlp_t *m);
+SPL_API void spl_mlp_free(spl_mlp_t *m);
+SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, double tol,
+                                                  int32_t max_iter, float *d_out, const int64_t *d_offsets,
+                                                  spl_report_t *h_reports, void *stream);
+
+/* The MLP's tensor-core GEMM on its own, for tests: D[M][N] = A[M][K] B[N][K]^T
+ * with row-major BF16 device matrices A, B and an FP32 device output D.
+ * M % 128 == 0, K % 64 == 0, N % 32 == 0. */
+SPL_API spl_status_t spl_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int32_t K, float *d_D,
+                                   void *stream);
+
 /* Materialised chains only: copy P (the paper's unnormalised P of Eq. 4/6,
  * lambda_j E_ij without the constant 1/(1 - e^-Lambda)) to d_P, row-major
  * [n_bins][n_bins].  SPL_EINVAL for fused chains. */
 SPL_API spl_status_t spl_matrix(spl_chain_t *c, float *d_P);
+
+/* Measurement: device time of one dense power-step pass of a chain (the
+ * TMA GEMV over the stored P, or the split regenerating column pass),
+ * averaged over `reps` back-to-back passes after one warm-up pass; CUDA
+ * events on the chain's stream.  Leaves the chain's iterate reset. */
+SPL_API spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass);
 
 /* Per-bin vectors of a built chain, for inspection: d_lambda (FP32 lambda(s_j)),
  * d_F (FP64 F(s_j)); either may be NULL.  h_Lambda (host, may be NULL) gets

@@ -353,6 +353,60 @@ extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_i
     return st;
 }
 
+extern "C" spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass) {
+    if (!c || reps < 1 || !ms_per_pass) return SPL_EINVAL;
+    cudaStream_t s = c->stream;
+    // a valid broadcast vector and an unfinished state so no kernel exits early
+    const FinishArgs fa = finish_args(c);
+    ChainState init{};
+    init.tol_err = 0.f;
+    init.max_iter = 1 << 30;
+    init.min_iter = 1 << 30;
+    SPL_CU(cudaMemcpyAsync(c->state, &init, sizeof(ChainState), cudaMemcpyHostToDevice, s));
+    SPL_CU(launch_init_iter(fa, nullptr, s));
+    cudaEvent_t e0, e1;
+    SPL_CU(cudaEventCreate(&e0));
+    SPL_CU(cudaEventCreate(&e1));
+    spl_status_t st = SPL_OK;
+    for (int i = 0; i < reps + 1 && st == SPL_OK; ++i) {
+        if (i == 1) cudaEventRecord(e0, s);   // first pass is a warm-up
+        if (c->mode == SPL_MATERIALIZED) {
+            GemvArgs g{};
+            g.N = c->N;
+            g.tiles_per_slab = c->tiles_per_slab;
+            g.total_tiles = c->total_tiles;
+            g.tiles_per_cta = c->tiles_per_cta;
+            g.c = c->v;
+            g.part = c->part;
+            g.state = c->state;
+            g.err_flag = c->err_flag;
+            if (launch_gemv(&c->tmap, g, c->gemv_grid, s) != cudaSuccess) st = SPL_ECUDA;
+        } else {
+            TriSplitArgs ta{};
+            ta.N = c->N;
+            ta.vlen = c->vlen;
+            ta.chunk = c->chunk;
+            ta.v = c->v;
+            ta.m = c->w;
+            ta.scal = c->scal;
+            ta.part = c->part;
+            ta.ld_part = c->ld_part;
+            ta.state = c->state;
+            if (launch_tri_split(ta, false, c->chunks, s) != cudaSuccess) st = SPL_ECUDA;
+        }
+    }
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPL_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "timing");
+    *ms_per_pass = ms / reps;
+    return SPL_OK;
+}
+
 extern "C" spl_status_t spl_matrix(spl_chain_t *c, float *d_P) {
     if (!c || !d_P || c->mode != SPL_MATERIALIZED) return SPL_EINVAL;
     SPL_CU(cudaMemcpy2DAsync(d_P, sizeof(float) * c->N, c->P, sizeof(float) * c->ld, sizeof(float) * c->N, c->N,
@@ -479,7 +533,8 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 
 // Launches the persistent batch kernel; out/warm are packed by caller order.
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
-                       int warm_logits, int min_iter, int threads_req, float *d_out, const int64_t *d_offsets,
+                       int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
+                       const int64_t *d_offsets,
                        cudaStream_t s, bool time_kernel = false) {
     const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
     if (threads != 256 && threads != 512 && threads != 1024) return SPL_EINVAL;
@@ -507,7 +562,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.n = n;
     a.counter = ws.counter;
     a.warm = d_warm;
-    a.warm_logits = warm_logits;
+    a.warm_kind = warm_kind;
+    a.warm_ld = warm_ld;
     a.out = d_out;
     a.offsets = d_offsets;
     a.reports = ws.reps;
@@ -565,11 +621,17 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     int nmax = 0;
     st = make_work_list(*ws, h_pixels, n, &nmax);
     if (st != SPL_OK) return st;
-    const int logits = opts ? opts->warm_is_logits : 0;
+    const int kind = opts ? opts->warm_kind : 0;
+    const int ld = opts ? opts->warm_ld : 0;
+    if (d_warm && (kind < 0 || kind > 2)) return SPL_EINVAL;
+    if (d_warm && kind == 2) {
+        for (int32_t k = 0; k < n; ++k)
+            if (ld < h_pixels[k].n_bins) return SPL_EINVAL;
+    }
     const int min_iter = opts ? opts->min_iter : 1;
     const int threads = opts ? opts->threads : 0;
     const bool timed = opts && opts->time_kernel;
-    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, logits, min_iter, threads, d_out, d_offsets, s, timed);
+    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the
@@ -605,7 +667,7 @@ extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, i
         if ((e = grow(&ws->d_warm, &ws->warm_cap, total)) != cudaSuccess) return status_of_alloc(e, "warm");
         SPL_CU(cudaMemcpyAsync(ws->d_warm, h_warm, sizeof(float) * total, cudaMemcpyHostToDevice, s));
     }
-    st = run_batch(*ws, n, nmax, tol, max_iter, h_warm ? ws->d_warm : nullptr, 0, 1, 0, ws->d_out, nullptr, s);
+    st = run_batch(*ws, n, nmax, tol, max_iter, h_warm ? ws->d_warm : nullptr, 0, 0, 1, 0, ws->d_out, nullptr, s);
     if (st != SPL_OK) return st;
     SPL_CU(cudaMemcpyAsync(h_out, ws->d_out, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
     if (h_reports) return collect_reports(*ws, n, h_reports, s);

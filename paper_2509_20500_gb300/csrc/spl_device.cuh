@@ -99,6 +99,15 @@ __device__ __forceinline__ void factors_bin(const PixelDev &p, const FluxConst &
     u = (float)(1.0 / e);
 }
 
+// Bin holding the pulse centre, floor(tau / Delta) clamped to [0, N): the
+// origin of the learned warm start's frame (the network's output index i
+// corresponds to bin (i + c) mod N).
+__host__ __device__ __forceinline__ int mlp_frame_shift(double t_r, double tau, int N) {
+    int c = (int)floor(tau * (double)N / t_r);
+    c = c < 0 ? 0 : c;
+    return c >= N ? N - 1 : c;
+}
+
 // ---------------------------------------------------------------- block reductions
 
 template <int NT>

@@ -200,7 +200,7 @@ __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f
 }
 
 __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlux &f, const double *t_lo,
-                                               const double *t_hi, int j, float &w, float &u) {
+                                               const double *t_hi, int j, float &w, float &u, float &lam_f) {
     const double g = t_hi[j >> 6] * t_lo[j & 63];                // exp(-B (j + 1/2) / N)
     const double s = ((double)j + 0.5) * f.delta;
     const double z = (s - p.tau) / p.sigma;
@@ -214,6 +214,7 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
         K = z > 0.0 ? f.K_hi : f.K_lo;
     }
     w = (float)(lam * K * g);
+    lam_f = (float)lam;
     // Row factor u_j = exp(F_j - Lambda/2) = lambda_j / w_j.  It cancels
     // exactly in the row-normalised matrix, so FP32 accuracy is enough.
     u = (float)lam / w;
@@ -262,12 +263,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(Ba
         batch_flux_setup(p, bf, s_tlo, s_thi, (N + 63) >> 6);
         const float eL = (float)exp(-bf.Lambda);
         __syncthreads();
+        const bool learned = a.warm != nullptr && a.warm_kind == 2;
         for (int j = tid; j < npad; j += NT) {
-            float w = 0.f, u = 0.f;
-            if (j < N) batch_flux_bin(p, bf, s_tlo, s_thi, j, w, u);
+            float w = 0.f, u = 0.f, lam = 0.f;
+            if (j < N) batch_flux_bin(p, bf, s_tlo, s_thi, j, w, u, lam);
             sv[j] = w;      // broadcast vector of the row pass
             gw[j] = w;
             gu[j] = u;
+            if (learned && j < N) spi[j] = logf(lam);   // flux prior of the learned start
         }
         __syncthreads();
 
@@ -292,11 +295,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(Ba
             }
         }
 
-        // ---- start vector
+        // ---- start vector: uniform, normalised weights, softmax of logits,
+        // or the learned start exp(z_{(j - c) mod N} + log lambda_j) / sum.
         float lsum = 0.f;
         if (a.warm == nullptr) {
             for (int j = tid; j < N; j += NT) spi[j] = 1.f / (float)N;
-        } else if (!a.warm_logits) {
+        } else if (a.warm_kind == 0) {
             for (int j = tid; j < N; j += NT) {
                 const float x = fmaxf(a.warm[off + j], 0.f);
                 spi[j] = x;
@@ -304,7 +308,23 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(Ba
             }
         } else {
             float mx = -INFINITY;
-            for (int j = tid; j < N; j += NT) mx = fmaxf(mx, a.warm[off + j]);
+            if (a.warm_kind == 1) {
+                for (int j = tid; j < N; j += NT) {
+                    const float e = a.warm[off + j];
+                    spi[j] = e;
+                    mx = fmaxf(mx, e);
+                }
+            } else {
+                const float *z = a.warm + (size_t)p.index * a.warm_ld;
+                const int c = mlp_frame_shift(p.t_r, p.tau, N);
+                for (int j = tid; j < N; j += NT) {
+                    int i = j - c;
+                    i += (i < 0) ? N : 0;
+                    const float e = z[i] + spi[j];
+                    spi[j] = e;
+                    mx = fmaxf(mx, e);
+                }
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0) red[wid] = mx;
@@ -317,7 +337,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(Ba
             __syncthreads();
             mx = s_scal[0];
             for (int j = tid; j < N; j += NT) {
-                const float x = __expf(a.warm[off + j] - mx);
+                const float x = __expf(spi[j] - mx);
                 spi[j] = x;
                 lsum += x;
             }

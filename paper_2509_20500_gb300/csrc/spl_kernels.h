@@ -24,8 +24,9 @@ struct BatchArgs {
     const PixelDev *px;      // sorted work list
     int n;
     int *counter;            // work-queue head, zero before launch
-    const float *warm;       // NULL, packed weights, or packed logits
-    int warm_logits;
+    const float *warm;       // NULL, or the warm start (see warm_kind)
+    int warm_kind;           // spl_warm_kind_t
+    int warm_ld;             // row stride of learned-frame logits
     float *out;              // packed output
     const int64_t *offsets;  // [n + 1] caller offsets by caller index, or NULL (use px.out_off)
     ReportDev *reports;      // [n] by caller index, may be NULL

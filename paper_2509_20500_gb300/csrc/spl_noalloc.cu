@@ -174,7 +174,8 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     a.n = n;
     a.counter = d_counter;
     a.warm = d_warm;
-    a.warm_logits = 0;
+    a.warm_kind = 0;
+    a.warm_ld = 0;
     a.out = d_out;
     a.offsets = d_offsets;
     a.reports = d_reps;

@@ -36,8 +36,11 @@ class spl_report_t(ctypes.Structure):
 
 
 class spl_batch_opts_t(ctypes.Structure):
-    _fields_ = [("warm_is_logits", ctypes.c_int32), ("min_iter", ctypes.c_int32),
+    _fields_ = [("warm_kind", ctypes.c_int32), ("warm_ld", ctypes.c_int32), ("min_iter", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32)]
+
+
+SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
 
 
 REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_l1", np.float32),
@@ -47,7 +50,9 @@ REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_
 # Symbols include/spl.h declares (checked by the CPU tests).
 EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_stationary_ex", "spl_batch_kernel_ms",
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
-            "spl_last_cuda_error", "spl_version"]
+            "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
+            "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
+            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass"]
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +108,32 @@ def lib():
         L.spl_last_cuda_error.restype = ctypes.c_char_p
         L.spl_version.argtypes = []
         L.spl_version.restype = ctypes.c_char_p
+        P = ctypes.POINTER(spl_pixel_t)
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.spl_mlp_create.argtypes = [i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+        L.spl_mlp_create.restype = ctypes.c_int
+        L.spl_mlp_param_count.argtypes = []
+        L.spl_mlp_param_count.restype = ctypes.c_int64
+        L.spl_mlp_set_params.argtypes = [vp, vp, ctypes.c_int64]
+        L.spl_mlp_set_params.restype = ctypes.c_int
+        L.spl_mlp_get_params.argtypes = [vp, vp, ctypes.c_int64]
+        L.spl_mlp_get_params.restype = ctypes.c_int
+        L.spl_mlp_forward.argtypes = [vp, P, i32, vp]
+        L.spl_mlp_forward.restype = ctypes.c_int
+        L.spl_mlp_loss_grad.argtypes = [vp, P, i32, vp, fp, vp]
+        L.spl_mlp_loss_grad.restype = ctypes.c_int
+        L.spl_mlp_train_step.argtypes = [vp, P, i32, vp, ctypes.c_float, ctypes.c_float, fp]
+        L.spl_mlp_train_step.restype = ctypes.c_int
+        L.spl_mlp_logits.argtypes = [vp]
+        L.spl_mlp_logits.restype = ctypes.c_void_p
+        L.spl_mlp_free.argtypes = [vp]
+        L.spl_mlp_free.restype = None
+        L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp]
+        L.spl_batch_stationary_learned.restype = ctypes.c_int
+        L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
+        L.spl_chain_time_pass.restype = ctypes.c_int
+        L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        L.spl_gemm_bf16.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -169,6 +200,12 @@ class Chain:
         _check(st, "spl_stationary", allow)
         return out, _reports_np(ctypes.addressof(rep), 1)[0]
 
+    def time_pass(self, reps: int = 20) -> float:
+        """Device ms of one dense power-step pass (spl_chain_time_pass)."""
+        ms = ctypes.c_float()
+        _check(lib().spl_chain_time_pass(self._c, int(reps), ctypes.byref(ms)), "spl_chain_time_pass")
+        return float(ms.value)
+
     def matrix(self):
         import torch
         P = torch.empty((self.n_bins, self.n_bins), dtype=torch.float32, device="cuda")
@@ -198,8 +235,8 @@ class Chain:
 
 
 def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
-                     warm_is_logits: bool = False, min_iter: int = 1, threads: int = 0, reports: bool = True,
-                     offsets=None, stream=None, time_kernel: bool = False, c_pixels=None):
+                     warm_kind: int = SPL_WARM_WEIGHTS, warm_ld: int = 0, min_iter: int = 1, threads: int = 0,
+                     reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None):
     """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
     import torch
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
@@ -211,7 +248,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
         out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
     arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
-    opts = spl_batch_opts_t(int(bool(warm_is_logits)), int(min_iter), int(threads), int(bool(time_kernel)))
+    opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)))
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
@@ -262,3 +299,87 @@ def batch_stationary_host(px: np.ndarray, tol: float = 1e-6, max_iter: int = 100
                                          reps, _stream_ptr(stream))
     _check(st, "spl_batch_stationary_host", (SPL_OK, SPL_ENOCONV))
     return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def gemm_bf16(A, B):
+    """D = A @ B^T with the library's tcgen05 kernel (A [M,K], B [N,K] bf16 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().spl_gemm_bf16(_dptr(A), _dptr(B), M, N, K, _dptr(D), _stream_ptr()), "spl_gemm_bf16")
+    return D
+
+
+class MLP:
+    """The learned warm-start network (spl_mlp_*)."""
+
+    N_OUT = 2000
+    LD = 2048
+
+    def __init__(self, max_batch: int, seed: int = 0, stream=None):
+        self._m = ctypes.c_void_p()
+        self._stream = _stream_ptr(stream)
+        self.max_batch = max_batch
+        _check(lib().spl_mlp_create(int(max_batch), int(seed), self._stream, ctypes.byref(self._m)), "spl_mlp_create")
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().spl_mlp_param_count())
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().spl_mlp_get_params(self._m, ctypes.c_void_p(out.ctypes.data), out.size), "spl_mlp_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().spl_mlp_set_params(self._m, ctypes.c_void_p(p.ctypes.data), p.size), "spl_mlp_set_params")
+
+    def forward(self, px: np.ndarray, out=None):
+        import torch
+        n = len(px)
+        if out is None:
+            out = torch.empty((n, self.LD), dtype=torch.float32, device="cuda")
+        _check(lib().spl_mlp_forward(self._m, pixels_to_c(px), n, _dptr(out)), "spl_mlp_forward")
+        return out
+
+    def loss_grad(self, px: np.ndarray, target, grads: bool = True):
+        loss = ctypes.c_float()
+        g = np.empty(self.param_count(), dtype=np.float32) if grads else None
+        _check(lib().spl_mlp_loss_grad(self._m, pixels_to_c(px), len(px), _dptr(target), ctypes.byref(loss),
+                                       ctypes.c_void_p(g.ctypes.data) if grads else None), "spl_mlp_loss_grad")
+        return float(loss.value), g
+
+    def train_step(self, c_px, n: int, target, lr: float, weight_decay: float = 0.0, want_loss: bool = False):
+        loss = ctypes.c_float()
+        _check(lib().spl_mlp_train_step(self._m, c_px, int(n), _dptr(target), float(lr), float(weight_decay),
+                                        ctypes.byref(loss) if want_loss else None), "spl_mlp_train_step")
+        return float(loss.value) if want_loss else None
+
+    def batch_stationary(self, px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, out=None, offsets=None,
+                         reports: bool = True, c_pixels=None):
+        import torch
+        n = len(px)
+        off = offsets_of(px)
+        if offsets is None:
+            offsets = torch.from_numpy(off).to("cuda")
+        if out is None:
+            out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
+        reps = (spl_report_t * max(1, n))() if reports else None
+        arr = pixels_to_c(px) if c_pixels is None else c_pixels
+        st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
+                                                _dptr(offsets), reps, self._stream)
+        _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))
+        return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+    def close(self):
+        if self._m:
+            lib().spl_mlp_free(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,126 @@
+"""Tensor-core GEMM and the learned warm-start network on the GPU.
+
+The GEMM (tcgen05, BF16 operands, FP32 accumulation) is compared with a
+plain PyTorch FP32 matmul of the same BF16 operands.  The network's loss and
+gradients are compared with the FP64 NumPy reference (oracle/mlp.py, pinned
+by finite differences) at the same parameters; BF16 weights and activations
+bound the agreement at about 1e-2 relative.  The learned batch path is
+checked against the FP64 oracle (1e-6 L1) and for what it gains in power
+steps over the plain start.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as ref_mlp
+from paper_2509_20500_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIZES = [5, 512, 512, 512, 512, 2000]
+
+
+@pytest.fixture(scope="module")
+def spl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_20500_gb300 import build, spl as S
+    build.build()
+    S.lib()
+    return S
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 256, 512), (384, 96, 192), (128, 2048, 512),
+                                   (2048, 512, 4096)])
+def test_gemm_bf16_vs_torch(spl, M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    D = spl.gemm_bf16(A, B)
+    ref = A.float() @ B.float().T
+    err = (D - ref).abs().max().item()
+    scale = (A.float().abs() @ B.float().abs().T).max().item()
+    assert err <= 1e-5 * scale, (err, scale)
+
+
+def _targets(n, seed):
+    rng = np.random.default_rng(seed)
+    t = rng.gamma(1.0, 1.0, (n, 2000))
+    return t / t.sum(axis=1, keepdims=True)
+
+
+def test_mlp_loss_and_gradients_vs_fp64_reference(spl):
+    px = W.array_pixels(96, seed=61)
+    pixels = W.as_dicts(px)
+    params = ref_mlp.init_params(SIZES, seed=4)
+    rng = np.random.default_rng(2)
+    params = [(Wm, rng.normal(0, 0.05, b.shape)) for Wm, b in params]
+    vec = ref_mlp.pack(params).astype(np.float32)
+    net = spl.MLP(max_batch=256, seed=0)
+    net.set_params(vec)
+    np.testing.assert_array_equal(net.get_params(), vec)
+    tg = _targets(len(px), 3)
+    loss, g = net.loss_grad(px, torch.tensor(tg, dtype=torch.float32, device="cuda"))
+    # reference at the FP32-rounded parameters
+    rparams = ref_mlp.unpack(vec.astype(np.float64), SIZES)
+    rloss, rgrads = ref_mlp.loss_and_grad(rparams, pixels, tg)
+    assert abs(loss - rloss) < 1e-2 * abs(rloss)
+    k = 0
+    for (dW, db) in rgrads:
+        for ref in (dW.ravel(), db):
+            got = g[k:k + ref.size].astype(np.float64)
+            k += ref.size
+            rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+            cos = float(got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-30))
+            assert rel < 3e-2 and cos > 0.999, (rel, cos)
+    assert k == g.size
+    net.close()
+
+
+def test_mlp_start_vector_vs_fp64_reference(spl):
+    """The batch kernel's learned start (logits rolled to the pulse bin plus
+    the log flux prior, softmax) against the reference start vector: one
+    power step from each agrees, and so does the start itself via
+    max_iter = 1 semantics (compare the network logits directly)."""
+    px = W.array_pixels(40, seed=62)
+    pixels = W.as_dicts(px)
+    params = ref_mlp.init_params(SIZES, seed=5)
+    vec = ref_mlp.pack(params).astype(np.float32)
+    net = spl.MLP(max_batch=128, seed=0)
+    net.set_params(vec)
+    z = net.forward(px).cpu().numpy()[:, :2000].astype(np.float64)
+    X = np.stack([ref_mlp.features(p)[0] for p in pixels])
+    rz, _ = ref_mlp.forward(ref_mlp.unpack(vec.astype(np.float64), SIZES), X)
+    assert np.abs(z - rz).max() < 2e-2 * np.abs(rz).max()
+    net.close()
+
+
+def test_learned_warm_start_gains_iterations(spl):
+    """Trained on stationary pmfs the method itself produces, the network's
+    start needs fewer power steps than the uniform start, and the result is
+    unchanged: the plain iteration still runs to the stop rule and agrees
+    with the FP64 oracle to 1e-6 L1."""
+    train = W.training(16384, seed=2)
+    tgt, off, _ = spl.batch_stationary(train, tol=1e-6)
+    tgt = tgt.view(len(train), 2000)
+    net = spl.MLP(max_batch=1024, seed=1)
+    c_all = [spl.pixels_to_c(train[i:i + 1024]) for i in range(0, len(train), 1024)]
+    step = 0
+    for epoch in range(12):
+        for b, cpx in enumerate(c_all):
+            lr = 2e-3 * min(1.0, (step + 1) / 50)
+            net.train_step(cpx, 1024, tgt[b * 1024:(b + 1) * 1024], lr=lr)
+            step += 1
+    torch.cuda.synchronize()
+    test = W.array_pixels(2048, seed=77)
+    plain, off, rp = spl.batch_stationary(test, tol=1e-6)
+    learned, off2, rl = net.batch_stationary(test, tol=1e-6)
+    assert np.all(rl["status"] == 0)
+    assert rl["iters"].mean() < rp["iters"].mean() - 0.5, (rl["iters"].mean(), rp["iters"].mean())
+    o_l = learned.cpu().numpy().astype(np.float64)
+    idx = W.sample_indices(len(test), 16, seed=9)
+    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(test[idx]), tol=1e-12)
+    for r, k in enumerate(idx):
+        assert np.abs(o_l[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() < 1e-6
+    net.close()

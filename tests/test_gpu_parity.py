@@ -236,7 +236,7 @@ def test_batch_warm_logits_and_weights(spl):
     ref, off, reps0 = spl.batch_stationary(px)
     r = ref.cpu().numpy().astype(np.float64)
     logits = torch.tensor(np.log(r), dtype=torch.float32, device="cuda")
-    o1, _, reps1 = spl.batch_stationary(px, warm=logits, warm_is_logits=True)
+    o1, _, reps1 = spl.batch_stationary(px, warm=logits, warm_kind=spl.SPL_WARM_LOGITS)
     o2, _, reps2 = spl.batch_stationary(px, warm=ref * 3.0)
     # a start already at the answer stops once the steps sit on the FP32 floor
     assert reps1["iters"].max() <= 8 and reps2["iters"].max() <= 8
