@@ -31,7 +31,23 @@ namespace spl {
 // acc_c += v_b * m_c(b) with the regenerated factor m_c(b).  Sums are
 // blocked: 128-term inner chains added into an outer accumulator.
 
-constexpr int kChain = 128;
+// Tuning knobs of the dense passes (compile-time): chunk length of the
+// compensated sums, FFMA chains per output, outputs per thread in the batch
+// kernel and its target blocks per SM.
+#ifndef SPL_KCHAIN
+#define SPL_KCHAIN 256
+#endif
+#ifndef SPL_NCH
+#define SPL_NCH 4
+#endif
+#ifndef SPL_BATCH_C
+#define SPL_BATCH_C 4
+#endif
+#ifndef SPL_BATCH_MINB
+#define SPL_BATCH_MINB 3
+#endif
+constexpr int kChain = SPL_KCHAIN;
+constexpr int kNch = SPL_NCH;
 
 // Compensated accumulation of a positive chunk sum x into (acc, comp):
 // TwoSum gives the exact rounding error of acc + x, which is carried in comp.
@@ -43,33 +59,51 @@ __device__ __forceinline__ void two_sum_acc(float &acc, float &comp, float x) {
     comp += e;
 }
 
+template <int C>
+__device__ __forceinline__ void chains_zero(float (&in)[kNch][C]) {
+#pragma unroll
+    for (int h = 0; h < kNch; ++h)
+#pragma unroll
+        for (int c = 0; c < C; ++c) in[h][c] = 0.f;
+}
+
+template <int C>
+__device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[C], float (&comp)[C]) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float t;
+        if (kNch == 4) t = (in[0][c] + in[1][c]) + (in[2][c] + in[3][c]);
+        else if (kNch == 2) t = in[0][c] + in[1][c];
+        else t = in[0][c];
+        two_sum_acc(acc[c], comp[c], t);
+    }
+}
+
 // Uniform-weight run over b in [lo, hi) (multiples of 4).  Each kChain-long
-// chunk is summed as four interleaved FFMA chains (one per float4 lane),
-// which are then added into the compensated outer accumulator.  Relative
-// rounding error per output ~1 FP32 unit roundoff instead of ~15 for one
-// sequential 2000-term chain.
+// chunk is summed in kNch interleaved FFMA chains (float4 lane e feeds chain
+// e % kNch), which are then added into the compensated outer accumulator:
+// relative rounding error per output about one FP32 unit roundoff instead of
+// ~15 for one sequential 2000-term chain.
 template <int C>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
                                         float (&acc)[C], float (&comp)[C]) {
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
     for (int b0 = lo; b0 < hi; b0 += kChain) {
         const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
-        float i0[C], i1[C], i2[C], i3[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
+        float in[kNch][C];
+        chains_zero<C>(in);
 #pragma unroll 8
         for (int q = 0; q < q1; ++q) {
             const float4 x = v4[(b0 >> 2) + q];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                i0[c] = fmaf(x.x, m[c], i0[c]);
-                i1[c] = fmaf(x.y, m[c], i1[c]);
-                i2[c] = fmaf(x.z, m[c], i2[c]);
-                i3[c] = fmaf(x.w, m[c], i3[c]);
+                in[0 % kNch][c] = fmaf(x.x, m[c], in[0 % kNch][c]);
+                in[1 % kNch][c] = fmaf(x.y, m[c], in[1 % kNch][c]);
+                in[2 % kNch][c] = fmaf(x.z, m[c], in[2 % kNch][c]);
+                in[3 % kNch][c] = fmaf(x.w, m[c], in[3 % kNch][c]);
             }
         }
-#pragma unroll
-        for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
+        chains_flush<C>(in, acc, comp);
     }
 }
 
@@ -98,12 +132,11 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         for (int c = 0; c < C; ++c) m[c] = kRowPass ? mhi[c] : mlo[c];
         tri_run<C>(v, b_lo, min(b_hi, base), m, acc, comp);
     }
-    // the span itself (one chunk of 32 C entries)
+    // the span itself (32 C entries, added as chunks of at most kChain)
     if (base >= b_lo && span_end <= b_hi) {
         const float4 *v4 = reinterpret_cast<const float4 *>(v);
-        float i0[C], i1[C], i2[C], i3[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) { i0[c] = 0.f; i1[c] = 0.f; i2[c] = 0.f; i3[c] = 0.f; }
+        float in[kNch][C];
+        chains_zero<C>(in);
 #pragma unroll
         for (int cb = 0; cb < C; ++cb) {
             // weights of the columns that are uniform over this block
@@ -125,21 +158,23 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
                         const bool n1 = kRowPass ? (t + 1 >= lane) : (t + 1 <= lane);
                         const bool n2 = kRowPass ? (t + 2 >= lane) : (t + 2 <= lane);
                         const bool n3 = kRowPass ? (t + 3 >= lane) : (t + 3 <= lane);
-                        i0[c] = fmaf(x.x, n0 ? mlo[c] : mhi[c], i0[c]);
-                        i1[c] = fmaf(x.y, n1 ? mlo[c] : mhi[c], i1[c]);
-                        i2[c] = fmaf(x.z, n2 ? mlo[c] : mhi[c], i2[c]);
-                        i3[c] = fmaf(x.w, n3 ? mlo[c] : mhi[c], i3[c]);
+                        in[0 % kNch][c] = fmaf(x.x, n0 ? mlo[c] : mhi[c], in[0 % kNch][c]);
+                        in[1 % kNch][c] = fmaf(x.y, n1 ? mlo[c] : mhi[c], in[1 % kNch][c]);
+                        in[2 % kNch][c] = fmaf(x.z, n2 ? mlo[c] : mhi[c], in[2 % kNch][c]);
+                        in[3 % kNch][c] = fmaf(x.w, n3 ? mlo[c] : mhi[c], in[3 % kNch][c]);
                     } else {
-                        i0[c] = fmaf(x.x, m[c], i0[c]);
-                        i1[c] = fmaf(x.y, m[c], i1[c]);
-                        i2[c] = fmaf(x.z, m[c], i2[c]);
-                        i3[c] = fmaf(x.w, m[c], i3[c]);
+                        in[0 % kNch][c] = fmaf(x.x, m[c], in[0 % kNch][c]);
+                        in[1 % kNch][c] = fmaf(x.y, m[c], in[1 % kNch][c]);
+                        in[2 % kNch][c] = fmaf(x.z, m[c], in[2 % kNch][c]);
+                        in[3 % kNch][c] = fmaf(x.w, m[c], in[3 % kNch][c]);
                     }
                 }
             }
+            if (((cb + 1) * 32) % kChain == 0 || cb == C - 1) {
+                chains_flush<C>(in, acc, comp);
+                chains_zero<C>(in);
+            }
         }
-#pragma unroll
-        for (int c = 0; c < C; ++c) two_sum_acc(acc[c], comp[c], (i0[c] + i1[c]) + (i2[c] + i3[c]));
     }
     // above the span: b > a for every owned a
     {
@@ -221,7 +256,7 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
 }
 
 template <int NT, int C>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : 1)) batch_fused_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fused_kernel(BatchArgs a) {
     extern __shared__ float4 smem4[];
     float *sv = reinterpret_cast<float *>(smem4);
     float *spi = sv + a.npad_max;
@@ -563,15 +598,26 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 constexpr int kGemvCols = 128;
 constexpr int kGemvRows = 32;
 constexpr int kGemvTileBytes = kGemvCols * kGemvRows * 4;
+constexpr int kGemvThreads = 256;      // 8 row groups x 32 column groups
+constexpr int kGemvMaxSmemC = 16384;   // row coefficients staged in shared memory up to this N
 
-template <int STAGES>
-__global__ void __launch_bounds__(kGemvCols) gemv_tma_kernel(const __grid_constant__ CUtensorMap tmap, GemvArgs a) {
+// 256 threads per CTA: thread (rg, cg) owns columns 4cg..4cg+3 of the slab and
+// rows 4rg..4rg+3 of every 32-row tile, so each tile is read from shared
+// memory with four 16-byte loads per thread.  The row coefficients c_i are
+// staged in shared memory once (when N <= 16384).  Per-thread partial sums
+// use TwoSum compensation across tiles; the 8 row groups are combined in
+// shared memory when the slab changes and at the end.
+template <int STAGES, bool kSmemC>
+__global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_constant__ CUtensorMap tmap, GemvArgs a) {
     extern __shared__ __align__(1024) uint8_t gsm[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+    float *cs = reinterpret_cast<float *>(tiles + (size_t)STAGES * kGemvTileBytes);
     __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ float red[8][kGemvCols];
     if (a.state && a.state->done) return;
 
     const int tid = threadIdx.x;
+    const int cg = tid & 31, rg = tid >> 5;
     const int per = a.tiles_per_cta;
     const int t0 = blockIdx.x * per;
     const int t1 = min(a.total_tiles, t0 + per);
@@ -595,36 +641,58 @@ __global__ void __launch_bounds__(kGemvCols) gemv_tma_kernel(const __grid_consta
     if (tid == 0) {
         for (int it = 0; it < STAGES && it < ntiles; ++it) issue(it);
     }
+    if (kSmemC) {
+        const int rows = a.tiles_per_slab * kGemvRows;
+        for (int i = tid; i < rows; i += kGemvThreads) cs[i] = (i < a.N) ? a.c[i] : 0.f;
+        __syncthreads();
+    }
     const int slab0 = t0 / a.tiles_per_slab;
     int cur_slab = slab0;
-    float acc = 0.f, comp = 0.f;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    auto flush = [&](int slab) {
+        // combine the 8 row groups of this slab's partial column sums
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[rg][4 * cg + q] = acc[q] + comp[q];
+        __syncthreads();
+        if (tid < kGemvCols) {
+            float y = 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) y += red[r][tid];
+            a.part[((size_t)blockIdx.x * 2 + (slab - slab0)) * kGemvCols + tid] = y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { acc[q] = 0.f; comp[q] = 0.f; }
+    };
     bool timed_out = false;
     int it = 0;
     for (; it < ntiles; ++it) {
         const int s = it % STAGES;
         const uint32_t parity = (uint32_t)((it / STAGES) & 1);
-        if (!mbar_wait(&full[s], parity)) { timed_out = true; break; }
         const int t = t0 + it;
         const int slab = t / a.tiles_per_slab;
         const int rt = t - slab * a.tiles_per_slab;
         if (slab != cur_slab) {
-            a.part[((size_t)blockIdx.x * 2 + (cur_slab - slab0)) * kGemvCols + tid] = acc + comp;
-            acc = 0.f;
-            comp = 0.f;
+            flush(cur_slab);
             cur_slab = slab;
         }
-        const float *tile = reinterpret_cast<const float *>(tiles + (size_t)s * kGemvTileBytes);
-        const int r0 = rt * kGemvRows;
-        float in0 = 0.f, in1 = 0.f;
+        if (!mbar_wait(&full[s], parity)) { timed_out = true; }
+        if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+        const float4 *tile = reinterpret_cast<const float4 *>(tiles + (size_t)s * kGemvTileBytes);
+        const int r0 = rt * kGemvRows + 4 * rg;
+        float in[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int r = 0; r < kGemvRows; r += 2) {
+        for (int r = 0; r < 4; ++r) {
             const int i = r0 + r;
-            const float c0 = (i < a.N) ? __ldg(a.c + i) : 0.f;
-            const float c1 = (i + 1 < a.N) ? __ldg(a.c + i + 1) : 0.f;
-            in0 = fmaf(c0, tile[r * kGemvCols + tid], in0);
-            in1 = fmaf(c1, tile[(r + 1) * kGemvCols + tid], in1);
+            const float c = kSmemC ? cs[i] : ((i < a.N) ? __ldg(a.c + i) : 0.f);
+            const float4 x = tile[(4 * rg + r) * (kGemvCols / 4) + cg];
+            in[0] = fmaf(c, x.x, in[0]);
+            in[1] = fmaf(c, x.y, in[1]);
+            in[2] = fmaf(c, x.z, in[2]);
+            in[3] = fmaf(c, x.w, in[3]);
         }
-        two_sum_acc(acc, comp, in0 + in1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) two_sum_acc(acc[q], comp[q], in[q]);
         __syncthreads();   // every thread is done with buffer s
         if (tid == 0 && it + STAGES < ntiles) issue(it + STAGES);
     }
@@ -638,7 +706,7 @@ __global__ void __launch_bounds__(kGemvCols) gemv_tma_kernel(const __grid_consta
         __syncthreads();
         return;
     }
-    a.part[((size_t)blockIdx.x * 2 + (cur_slab - slab0)) * kGemvCols + tid] = acc + comp;
+    flush(cur_slab);
 }
 
 // ======================================================================
@@ -822,17 +890,17 @@ int batch_threads_for(int nmax) { return nmax <= 4096 ? 256 : 1024; }
 
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
     if (threads == 512) {
-        auto k = batch_fused_kernel<512, 4>;
+        auto k = batch_fused_kernel<512, SPL_BATCH_C>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<grid, 512, smem, s>>>(a);
     } else if (threads == 256) {
-        auto k = batch_fused_kernel<256, 4>;
+        auto k = batch_fused_kernel<256, SPL_BATCH_C>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<grid, 256, smem, s>>>(a);
     } else {
-        auto k = batch_fused_kernel<1024, 4>;
+        auto k = batch_fused_kernel<1024, SPL_BATCH_C>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<grid, 1024, smem, s>>>(a);
@@ -842,7 +910,7 @@ cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem,
 
 template <int NT>
 static cudaError_t occupancy_one(size_t smem, int *bps) {
-    auto k = batch_fused_kernel<NT, 4>;
+    auto k = batch_fused_kernel<NT, SPL_BATCH_C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, smem);
@@ -854,7 +922,7 @@ cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm) {
     return occupancy_one<1024>(smem, blocks_per_sm);
 }
 
-int batch_pad_len(int n) { return pad_len(n, 4); }
+int batch_pad_len(int n) { return pad_len(n, SPL_BATCH_C); }
 
 // v, pi, rho (+ w, u, y, d1, d2 when in shared memory) and the FP64 table of
 // 64-bin blocks of the geometric flux factor.
@@ -881,16 +949,26 @@ cudaError_t launch_build_matrix(int N, int l, int ld, const float *w, const floa
     return cudaGetLastError();
 }
 
-constexpr int kGemvStages = 8;
+constexpr int kGemvStages = 10;
 
-size_t gemv_smem_bytes() { return (size_t)kGemvStages * kGemvTileBytes + 1024; }
+size_t gemv_smem_bytes() { return (size_t)kGemvStages * kGemvTileBytes + 1024 + (size_t)kGemvMaxSmemC * 4; }
 
 cudaError_t launch_gemv(const CUtensorMap *map, const GemvArgs &a, int grid, cudaStream_t s) {
-    auto k = gemv_tma_kernel<kGemvStages>;
-    const size_t smem = gemv_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kGemvCols, smem, s>>>(*map, a);
+    const bool smem_c = a.tiles_per_slab * kGemvRows <= kGemvMaxSmemC;
+    const size_t smem = (size_t)kGemvStages * kGemvTileBytes + 1024 +
+                        (smem_c ? (size_t)a.tiles_per_slab * kGemvRows * 4 : 0);
+    cudaError_t e;
+    if (smem_c) {
+        auto k = gemv_tma_kernel<kGemvStages, true>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kGemvThreads, smem, s>>>(*map, a);
+    } else {
+        auto k = gemv_tma_kernel<kGemvStages, false>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kGemvThreads, smem, s>>>(*map, a);
+    }
     return cudaGetLastError();
 }
 

@@ -27,14 +27,15 @@ def make_training_set(n: int = 200_000, seed: int = 2, tol: float = 1e-6):
 
 
 def train(px, targets, epochs: int = 20, batch: int = 4096, lr: float = 2e-3, warmup: int = 100,
-          weight_decay: float = 0.0, seed: int = 1, net=None, log=None):
+          weight_decay: float = 0.0, seed: int = 1, net=None, log=None, max_batch: int = 0):
     """Fits the network on (px, targets) with a linear warm-up then cosine
-    learning-rate decay.  Returns the network."""
+    learning-rate decay.  Returns the network; max_batch (>= batch) sizes it
+    for later inference on larger batches."""
     import torch
     n = len(px)
     nb = n // batch
     if net is None:
-        net = spl.MLP(max_batch=batch, seed=seed)
+        net = spl.MLP(max_batch=max(batch, max_batch), seed=seed)
     rng = np.random.default_rng(seed)
     total = epochs * nb
     step = 0
