@@ -308,6 +308,34 @@ def run_gpu(args):
                       "iters_mean": float(reps_plain["iters"].mean()), "iters_max": int(reps_plain["iters"].max()),
                       "kernel_ms": statistics.median(plain_kern)}
 
+    # the O(N) structured form of the same power step (reported beside the
+    # dense path, never as its number): plain and learned starts
+    if not args.no_structured:
+        st = {}
+        def s_plain():
+            return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=False,
+                                        c_pixels=c_px, time_kernel=True, pass_kind=spl.SPL_PASS_STRUCTURED)
+        _, _, r_sp = spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=True,
+                                          c_pixels=c_px, pass_kind=spl.SPL_PASS_STRUCTURED)
+        for _ in range(args.warmup):
+            s_plain()
+        sms, skern = timed_steps(s_plain, args.steps, flush, stream, spl.batch_kernel_ms)
+        st["plain"] = {"value": world * n / (statistics.mean(sms) / 1e3), "ms_per_step": statistics.mean(sms),
+                       "kernel_ms": statistics.median(skern), "iters_mean": float(r_sp["iters"].mean())}
+        if learned:
+            def s_learned():
+                return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=False,
+                                            c_pixels=c_px, pass_kind=spl.SPL_PASS_STRUCTURED)
+            _, _, r_sl = net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=True,
+                                              c_pixels=c_px, pass_kind=spl.SPL_PASS_STRUCTURED)
+            for _ in range(args.warmup):
+                s_learned()
+            lms, lkern = timed_steps(s_learned, args.steps, flush, stream, spl.batch_kernel_ms)
+            st["learned"] = {"value": world * n / (statistics.mean(lms) / 1e3), "ms_per_step": statistics.mean(lms),
+                             "kernel_ms": statistics.median(lkern), "iters_mean": float(r_sl["iters"].mean())}
+        st["note"] = "O(N) scan form of the power step (Eq. 6 triangular structure); same pmfs, not the dense-path number"
+        extra["structured"] = st
+
     # materialised vs matrix-free power step on one N = 10000 pixel (400 MB P)
     if not args.no_highres and rank == 0:
         hp = W.pixel(10000, 75.0, 30.0, 0.3, 0.5, 0.5)
@@ -395,6 +423,7 @@ def main():
     ap.add_argument("--pixels", type=int, default=0, help="use only the first P pixels (profiling)")
     ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
     ap.add_argument("--no-highres", action="store_true")
+    ap.add_argument("--no-structured", action="store_true")
     ap.add_argument("--train-pixels", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()

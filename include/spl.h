@@ -139,6 +139,14 @@ typedef enum {
                                start_j ~ exp(z[(j - c) mod N] + log lambda(s_j)), c = floor(tau / Delta) */
 } spl_warm_kind_t;
 
+/* Form of the power step of the batch kernel. */
+typedef enum {
+    SPL_PASS_DENSE = 0,       /* every entry of P~ regenerated and used (N^2 FFMA per step) */
+    SPL_PASS_STRUCTURED = 1,  /* the same step through the triangular structure of Eq. 6:
+                                 y_j = w_j (P_j + e^-Lambda (T - P_j)) with P a prefix sum
+                                 (O(N) per step; row sums by prefix and suffix scans) */
+} spl_pass_kind_t;
+
 /* Options for spl_batch_stationary_ex. */
 typedef struct {
     int32_t warm_kind;        /* spl_warm_kind_t, used when d_warm != NULL */
@@ -146,6 +154,7 @@ typedef struct {
     int32_t min_iter;         /* steps always taken before the stop rule may fire (>= 1) */
     int32_t threads;          /* threads per block, 0 = library default */
     int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
+    int32_t pass_kind;        /* spl_pass_kind_t */
 } spl_batch_opts_t;
 
 /* spl_batch_stationary with options (opts may be NULL for the defaults). */
@@ -234,7 +243,8 @@ SPL_API const float *spl_mlp_logits(spl_mlp_t *m);
 SPL_API void spl_mlp_free(spl_mlp_t *m);
 SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, double tol,
                                                   int32_t max_iter, float *d_out, const int64_t *d_offsets,
-                                                  spl_report_t *h_reports, void *stream);
+                                                  spl_report_t *h_reports, void *stream,
+                                                  const spl_batch_opts_t *opts /* nullable; warm fields ignored */);
 
 /* The MLP's tensor-core GEMM on its own, for tests: D[M][N] = A[M][K] B[N][K]^T
  * with row-major BF16 device matrices A, B and an FP32 device output D.

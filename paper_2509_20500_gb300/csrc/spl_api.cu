@@ -204,18 +204,19 @@ extern "C" spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *s
         if (e != cudaSuccess) { chain_release(c); return e == cudaErrorMemoryAllocation ? SPL_ENOMEM : cuda_fail(e, "P"); }
         e = launch_build_matrix(N, d.l, c->ld, c->w, c->u, c->scal, c->P, c->rowsum, num_sms_current(), s);
         if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "build_matrix"); }
-        // TMA descriptor over P: dims {cols, rows}, row pitch ld floats, 128 x 32 boxes.
+        // TMA descriptor over P: dims {cols, rows}, row pitch ld floats, slab-wide x 32-row boxes.
+        const int SC = gemv_slab_cols();
         auto enc = get_encode_tiled();
         if (!enc) { chain_release(c); return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
         cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
         cuuint64_t gstride[1] = {(cuuint64_t)c->ld * sizeof(float)};
-        cuuint32_t box[2] = {128, 32};
+        cuuint32_t box[2] = {(cuuint32_t)SC, 32};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->P, gdim, gstride, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { chain_release(c); return cuda_fail(cudaErrorInvalidValue, "tensor map encode"); }
-        const int slabs = (N + 127) / 128;
+        const int slabs = (N + SC - 1) / SC;
         c->tiles_per_slab = (N + 31) / 32;
         c->total_tiles = slabs * c->tiles_per_slab;
         int grid = num_sms_current();
@@ -223,9 +224,9 @@ extern "C" spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *s
         c->tiles_per_cta = (c->total_tiles + grid - 1) / grid;
         if (c->tiles_per_cta > c->tiles_per_slab) c->tiles_per_cta = c->tiles_per_slab;
         c->gemv_grid = (c->total_tiles + c->tiles_per_cta - 1) / c->tiles_per_cta;
-        e = dalloc(&c->part, (size_t)c->gemv_grid * 2 * 128);
+        e = dalloc(&c->part, (size_t)c->gemv_grid * 2 * SC);
         if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "part"); }
-        e = cudaMemsetAsync(c->part, 0, sizeof(float) * (size_t)c->gemv_grid * 2 * 128, s);
+        e = cudaMemsetAsync(c->part, 0, sizeof(float) * (size_t)c->gemv_grid * 2 * SC, s);
         if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "memset part"); }
     } else {
         e = dalloc(&c->part, (size_t)c->chunks * c->ld_part);
@@ -535,7 +536,7 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
-                       cudaStream_t s, bool time_kernel = false) {
+                       cudaStream_t s, bool time_kernel = false, int structured = 0) {
     const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
     if (threads != 256 && threads != 512 && threads != 1024) return SPL_EINVAL;
     const int npad = batch_pad_len(nmax);
@@ -573,6 +574,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);
+    a.structured = structured;
     if (time_kernel) {
         if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
@@ -631,7 +633,10 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     const int min_iter = opts ? opts->min_iter : 1;
     const int threads = opts ? opts->threads : 0;
     const bool timed = opts && opts->time_kernel;
-    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed);
+    const int structured = opts ? opts->pass_kind : 0;
+    if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed,
+                   structured);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the

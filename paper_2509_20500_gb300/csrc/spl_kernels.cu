@@ -194,6 +194,63 @@ __host__ __device__ __forceinline__ int pad_len(int n, int C) {
 }
 
 // ======================================================================
+// Block-wide scans for the structured (O(N)) power step
+// ======================================================================
+//
+// Inclusive scan of v[0..n) into out[0..n) in tiles of NT*8 consecutive
+// elements (thread t holds 8 consecutive ones), carrying the running sum
+// between tiles; rev = true scans from the end (suffix sums).  Returns the
+// total.  red needs 2 * (NT/32) + 2 floats.
+template <int NT>
+__device__ float block_scan(const float *v, float *out, int n, bool rev, float *red) {
+    constexpr int IT = 8, NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float carry = 0.f;
+    for (int t0 = 0; t0 < n; t0 += NT * IT) {
+        float x[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = t0 + tid * IT + i;
+            x[i] = (e < n) ? v[rev ? n - 1 - e : e] : 0.f;
+        }
+#pragma unroll
+        for (int i = 1; i < IT; ++i) x[i] += x[i - 1];
+        float sc = x[IT - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += y;
+        }
+        float lane_ex = __shfl_up_sync(0xffffffffu, sc, 1);
+        if (lane == 0) lane_ex = 0.f;
+        if (lane == 31) red[wid] = sc;
+        __syncthreads();
+        if (wid == 0) {
+            float ws = (lane < NW) ? red[lane] : 0.f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += y;
+            }
+            float wex = __shfl_up_sync(0xffffffffu, ws, 1);
+            if (lane == 0) wex = 0.f;
+            if (lane < NW) red[NW + 2 + lane] = wex;
+            if (lane == NW - 1) red[NW] = ws;
+        }
+        __syncthreads();
+        const float off = carry + red[NW + 2 + wid] + lane_ex;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = t0 + tid * IT + i;
+            if (e < n) out[rev ? n - 1 - e : e] = x[i] + off;
+        }
+        carry += red[NW];
+        __syncthreads();
+    }
+    return carry;
+}
+
+// ======================================================================
 // K5: persistent batch driver with the per-CTA matrix-free step
 // ======================================================================
 //
@@ -216,7 +273,11 @@ __host__ __device__ __forceinline__ int pad_len(int n, int C) {
 // G_j is one of two constants) a bin costs two FP64 products instead of an
 // FP64 exp; inside the pulse the first factor is an FP64 exp of its own.
 struct BatchFlux {
-    double Phi0, Lambda, gnorm, delta, beta, K_lo, K_hi, bg;
+    double Phi0, Lambda, gnorm, delta, beta, inv_sigma, bg;
+    double bgK_lo, bgK_hi;   // bg * exp(Lambda/2 - S G) on either side of the pulse
+    double K_half;           // exp(Lambda/2)
+    float bg_f;
+    int j_lo, j_hi;          // bins with |z| <= 9 (the pulse); the rest are tail bins
 };
 
 __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f, double *t_lo, double *t_hi,
@@ -227,32 +288,40 @@ __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f
     f.gnorm = fc.gnorm;
     f.delta = fc.delta;
     f.beta = p.B / (double)p.N;
-    f.K_lo = exp(0.5 * fc.Lambda + p.S * fc.Phi0);             // G = -Phi0 (left of the pulse)
-    f.K_hi = exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));     // G = 1 - Phi0 (right of the pulse)
+    f.inv_sigma = 1.0 / p.sigma;
     f.bg = p.B / p.t_r;
+    f.bg_f = (float)f.bg;
+    f.bgK_lo = f.bg * exp(0.5 * fc.Lambda + p.S * fc.Phi0);             // G = -Phi0 (left of the pulse)
+    f.bgK_hi = f.bg * exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));     // G = 1 - Phi0 (right of the pulse)
+    f.K_half = exp(0.5 * fc.Lambda);
+    // pulse bins: s_j within 9 sigma of tau, i.e. j in [(tau - 9 sigma)/Delta - 1/2, (tau + 9 sigma)/Delta - 1/2]
+    const double lo = (p.tau - kTailZ * p.sigma) / fc.delta - 0.5;
+    const double hi = (p.tau + kTailZ * p.sigma) / fc.delta - 0.5;
+    f.j_lo = lo < 0.0 ? 0 : (int)ceil(lo);
+    f.j_hi = hi >= (double)(p.N - 1) ? p.N - 1 : (int)floor(hi);
     for (int b = threadIdx.x; b < 64; b += blockDim.x) t_lo[b] = exp(-f.beta * ((double)b + 0.5));
     for (int a = threadIdx.x; a < nblk; a += blockDim.x) t_hi[a] = exp(-f.beta * (64.0 * (double)a));
 }
 
+// Factors of bin j (see batch_flux_setup): two FP64 products outside the
+// pulse, the FP64 erfc/exp evaluation inside it.
 __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlux &f, const double *t_lo,
                                                const double *t_hi, int j, float &w, float &u, float &lam_f) {
     const double g = t_hi[j >> 6] * t_lo[j & 63];                // exp(-B (j + 1/2) / N)
-    const double s = ((double)j + 0.5) * f.delta;
-    const double z = (s - p.tau) / p.sigma;
-    double lam, K;
-    if (fabs(z) <= kTailZ) {
-        const double G = std_cdf(z) - f.Phi0;
-        lam = p.S * exp(-0.5 * z * z) * f.gnorm + f.bg;
-        K = exp(0.5 * f.Lambda - p.S * G);
+    if (j < f.j_lo || j > f.j_hi) {
+        w = (float)((j < f.j_lo ? f.bgK_lo : f.bgK_hi) * g);
+        lam_f = f.bg_f;
     } else {
-        lam = f.bg;
-        K = z > 0.0 ? f.K_hi : f.K_lo;
+        const double s = ((double)j + 0.5) * f.delta;
+        const double z = (s - p.tau) * f.inv_sigma;
+        const double G = std_cdf(z) - f.Phi0;
+        const double lam = p.S * exp(-0.5 * z * z) * f.gnorm + f.bg;
+        w = (float)(lam * exp(0.5 * f.Lambda - p.S * G) * g);
+        lam_f = (float)lam;
     }
-    w = (float)(lam * K * g);
-    lam_f = (float)lam;
     // Row factor u_j = exp(F_j - Lambda/2) = lambda_j / w_j.  It cancels
     // exactly in the row-normalised matrix, so FP32 accuracy is enough.
-    u = (float)lam / w;
+    u = lam_f / w;
 }
 
 template <int NT, int C>
@@ -309,7 +378,16 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
         }
         __syncthreads();
 
-        // ---- row sums r'_k (dense row pass), rho_k = u_k / r'_k
+        // ---- row sums r'_k, rho_k = u_k / r'_k
+        if (a.structured) {
+            // r'_k / u_k = sum_{j >= k} w_j + eL sum_{j < k} w_j: an inclusive
+            // suffix scan and an inclusive prefix scan of w (prefix - w_k is the
+            // exclusive prefix, whose rounding is damped by eL).
+            block_scan<NT>(gw, gy, N, false, red);      // gy = prefix
+            block_scan<NT>(gw, sv, N, true, red);       // sv = suffix
+            for (int k = tid; k < N; k += NT) srho[k] = 1.f / (sv[k] + eL * (gy[k] - gw[k]));
+            __syncthreads();
+        } else {
         for (int g = 0; g < ngroups; ++g) {
             const int base = (g * NW + wid) * 32 * C;
             if (base < N) {
@@ -328,6 +406,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
                     if (k < N) srho[k] = mlo[c] / r[c];
                 }
             }
+        }
         }
 
         // ---- start vector: uniform, normalised weights, softmax of logits,
@@ -403,6 +482,16 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
             }
             __syncthreads();
             float ysum = 0.f;
+            if (a.structured) {
+                // y_j = w_j (P_j + eL (T - P_j)), P = inclusive prefix of h, T = sum h
+                const float T = block_scan<NT>(sv, gy, N, false, red);
+                for (int j = tid; j < N; j += NT) {
+                    const float P = gy[j];
+                    const float y = gw[j] * fmaf(eL, T - P, P);
+                    gy[j] = y;
+                    ysum += y;
+                }
+            } else {
             for (int g = 0; g < ngroups; ++g) {
                 const int base = (g * NW + wid) * 32 * C;
                 if (base < N) {
@@ -421,6 +510,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
                         if (j < N) { gy[j] = y[c]; ysum += y[c]; }
                     }
                 }
+            }
             }
             const float s = block_sum<NT>(ysum, red);   // also orders the y writes before the reads
             const float inv = 1.f / s;
@@ -595,17 +685,26 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-constexpr int kGemvCols = 128;
+#ifndef SPL_GEMV_COLS
+#define SPL_GEMV_COLS 256
+#endif
+#ifndef SPL_GEMV_STAGES
+#define SPL_GEMV_STAGES 4
+#endif
+constexpr int kGemvCols = SPL_GEMV_COLS;     // slab width (columns per TMA box)
 constexpr int kGemvRows = 32;
 constexpr int kGemvTileBytes = kGemvCols * kGemvRows * 4;
-constexpr int kGemvThreads = 256;      // 8 row groups x 32 column groups
+constexpr int kGemvThreads = 256;
+constexpr int kGemvCG = kGemvCols / 4;       // column groups of 4 (one float4)
+constexpr int kGemvRG = kGemvThreads / kGemvCG;
+constexpr int kGemvRowsPerThread = kGemvRows / kGemvRG;
 constexpr int kGemvMaxSmemC = 16384;   // row coefficients staged in shared memory up to this N
 
 // 256 threads per CTA: thread (rg, cg) owns columns 4cg..4cg+3 of the slab and
-// rows 4rg..4rg+3 of every 32-row tile, so each tile is read from shared
-// memory with four 16-byte loads per thread.  The row coefficients c_i are
-// staged in shared memory once (when N <= 16384).  Per-thread partial sums
-// use TwoSum compensation across tiles; the 8 row groups are combined in
+// rows rg*R .. rg*R+R-1 of every 32-row tile (R = rows per thread), so each
+// tile is read from shared memory with 16-byte loads.  The row coefficients
+// c_i are staged in shared memory once (when N <= 16384).  Per-thread partial
+// sums use TwoSum compensation across tiles; the row groups are combined in
 // shared memory when the slab changes and at the end.
 template <int STAGES, bool kSmemC>
 __global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_constant__ CUtensorMap tmap, GemvArgs a) {
@@ -613,11 +712,11 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_con
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
     float *cs = reinterpret_cast<float *>(tiles + (size_t)STAGES * kGemvTileBytes);
     __shared__ __align__(8) uint64_t full[STAGES];
-    __shared__ float red[8][kGemvCols];
+    __shared__ float red[kGemvRG][kGemvCols];
     if (a.state && a.state->done) return;
 
     const int tid = threadIdx.x;
-    const int cg = tid & 31, rg = tid >> 5;
+    const int cg = tid % kGemvCG, rg = tid / kGemvCG;
     const int per = a.tiles_per_cta;
     const int t0 = blockIdx.x * per;
     const int t1 = min(a.total_tiles, t0 + per);
@@ -654,11 +753,11 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_con
 #pragma unroll
         for (int q = 0; q < 4; ++q) red[rg][4 * cg + q] = acc[q] + comp[q];
         __syncthreads();
-        if (tid < kGemvCols) {
+        for (int col = tid; col < kGemvCols; col += kGemvThreads) {
             float y = 0.f;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) y += red[r][tid];
-            a.part[((size_t)blockIdx.x * 2 + (slab - slab0)) * kGemvCols + tid] = y;
+            for (int r = 0; r < kGemvRG; ++r) y += red[r][col];
+            a.part[((size_t)blockIdx.x * 2 + (slab - slab0)) * kGemvCols + col] = y;
         }
         __syncthreads();
 #pragma unroll
@@ -679,13 +778,13 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_con
         if (!mbar_wait(&full[s], parity)) { timed_out = true; }
         if (__syncthreads_or(timed_out)) { timed_out = true; break; }
         const float4 *tile = reinterpret_cast<const float4 *>(tiles + (size_t)s * kGemvTileBytes);
-        const int r0 = rt * kGemvRows + 4 * rg;
+        const int r0 = rt * kGemvRows + kGemvRowsPerThread * rg;
         float in[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < kGemvRowsPerThread; ++r) {
             const int i = r0 + r;
             const float c = kSmemC ? cs[i] : ((i < a.N) ? __ldg(a.c + i) : 0.f);
-            const float4 x = tile[(4 * rg + r) * (kGemvCols / 4) + cg];
+            const float4 x = tile[(kGemvRowsPerThread * rg + r) * (kGemvCols / 4) + cg];
             in[0] = fmaf(c, x.x, in[0]);
             in[1] = fmaf(c, x.y, in[1]);
             in[2] = fmaf(c, x.z, in[2]);
@@ -949,7 +1048,9 @@ cudaError_t launch_build_matrix(int N, int l, int ld, const float *w, const floa
     return cudaGetLastError();
 }
 
-constexpr int kGemvStages = 10;
+constexpr int kGemvStages = SPL_GEMV_STAGES;
+
+int gemv_slab_cols() { return kGemvCols; }
 
 size_t gemv_smem_bytes() { return (size_t)kGemvStages * kGemvTileBytes + 1024 + (size_t)kGemvMaxSmemC * 4; }
 

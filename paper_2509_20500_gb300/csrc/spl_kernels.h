@@ -36,6 +36,7 @@ struct BatchArgs {
     float tol_err;
     int max_iter;
     int min_iter;
+    int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
 };
 
 struct GemvArgs {
@@ -88,6 +89,7 @@ cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam,
 cudaError_t launch_build_matrix(int N, int l, int ld, const float *w, const float *u, const double *scal, float *P,
                                 float *rowsum, int num_sms, cudaStream_t s);
 size_t gemv_smem_bytes();
+int gemv_slab_cols();
 cudaError_t launch_gemv(const CUtensorMap *map, const GemvArgs &a, int grid, cudaStream_t s);
 
 int split_cols_per_cta();

@@ -803,7 +803,8 @@ extern "C" const float *spl_mlp_logits(spl_mlp_t *m) { return m ? m->logits : nu
 
 extern "C" spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, double tol,
                                                      int32_t max_iter, float *d_out, const int64_t *d_offsets,
-                                                     spl_report_t *h_reports, void *stream) {
+                                                     spl_report_t *h_reports, void *stream,
+                                                     const spl_batch_opts_t *opts) {
     if (!m || n < 1 || !h_pixels) return SPL_EINVAL;
     if (stream != static_cast<void *>(m->stream)) return SPL_EINVAL;
     // Logits of the whole batch, produced chunk by chunk (max_batch rows at a
@@ -826,9 +827,10 @@ extern "C" spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pix
         if ((st = forward(m, c, false, m->warm + (size_t)k0 * kOutPad)) != SPL_OK) return st;
     }
     spl_batch_opts_t o{};
+    if (opts) o = *opts;
     o.warm_kind = SPL_WARM_LEARNED;
     o.warm_ld = kOutPad;
-    o.min_iter = 1;
+    if (o.min_iter < 1) o.min_iter = 1;
     o.time_kernel = 1;   // spl_batch_kernel_ms then reports this call's batch kernel
     spl_status_t st = spl_batch_stationary_ex(h_pixels, n, tol, max_iter, m->warm, d_out, d_offsets, h_reports,
                                               stream, &o);

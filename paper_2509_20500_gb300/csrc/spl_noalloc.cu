@@ -185,6 +185,7 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = 1;
+    a.structured = 0;
     if (launch_batch(a, threads, grid, smem, s) != cudaSuccess) return SPL_ECUDA;
 
     if (!h_reports) return SPL_OK;

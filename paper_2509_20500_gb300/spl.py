@@ -37,10 +37,11 @@ class spl_report_t(ctypes.Structure):
 
 class spl_batch_opts_t(ctypes.Structure):
     _fields_ = [("warm_kind", ctypes.c_int32), ("warm_ld", ctypes.c_int32), ("min_iter", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32), ("pass_kind", ctypes.c_int32)]
 
 
 SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
+SPL_PASS_DENSE, SPL_PASS_STRUCTURED = 0, 1
 
 
 REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_l1", np.float32),
@@ -128,7 +129,8 @@ def lib():
         L.spl_mlp_logits.restype = ctypes.c_void_p
         L.spl_mlp_free.argtypes = [vp]
         L.spl_mlp_free.restype = None
-        L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp]
+        L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp,
+                                                   ctypes.POINTER(spl_batch_opts_t)]
         L.spl_batch_stationary_learned.restype = ctypes.c_int
         L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.spl_chain_time_pass.restype = ctypes.c_int
@@ -236,7 +238,8 @@ class Chain:
 
 def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
                      warm_kind: int = SPL_WARM_WEIGHTS, warm_ld: int = 0, min_iter: int = 1, threads: int = 0,
-                     reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None):
+                     reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None,
+                     pass_kind: int = SPL_PASS_DENSE):
     """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
     import torch
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
@@ -248,7 +251,8 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
         out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
     arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
-    opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)))
+    opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)),
+                            int(pass_kind))
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
@@ -358,7 +362,7 @@ class MLP:
         return float(loss.value) if want_loss else None
 
     def batch_stationary(self, px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, out=None, offsets=None,
-                         reports: bool = True, c_pixels=None):
+                         reports: bool = True, c_pixels=None, pass_kind: int = SPL_PASS_DENSE):
         import torch
         n = len(px)
         off = offsets_of(px)
@@ -368,8 +372,9 @@ class MLP:
             out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
+        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind))
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
-                                                _dptr(offsets), reps, self._stream)
+                                                _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))
         return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
 

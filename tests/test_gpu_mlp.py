@@ -124,3 +124,29 @@ def test_learned_warm_start_gains_iterations(spl):
     for r, k in enumerate(idx):
         assert np.abs(o_l[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() < 1e-6
     net.close()
+
+
+def test_learned_start_with_structured_step(spl):
+    """The learned warm start also feeds the O(N) form of the step; results
+    match the dense form within the parity tolerance."""
+    train = W.training(8192, seed=2)
+    tgt, _, _ = spl.batch_stationary(train, tol=1e-6)
+    net = spl.MLP(max_batch=1024, seed=1)
+    tg = tgt.view(len(train), 2000)
+    for ep in range(4):
+        for b in range(8):
+            net.train_step(spl.pixels_to_c(train[b * 1024:(b + 1) * 1024]), 1024, tg[b * 1024:(b + 1) * 1024],
+                           lr=2e-3)
+    test = W.array_pixels(1500, seed=78)
+    d, off, rd = net.batch_stationary(test, tol=1e-6)
+    s, _, rs = net.batch_stationary(test, tol=1e-6, pass_kind=spl.SPL_PASS_STRUCTURED)
+    assert np.all(rs["status"] == 0)
+    d, s = d.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+    # each form is within 1e-6 of the exact pmf, so they agree within 2e-6
+    for k in range(len(test)):
+        assert np.abs(d[off[k]:off[k + 1]] - s[off[k]:off[k + 1]]).sum() < 2e-6
+    idx = W.sample_indices(len(test), 12, seed=10)
+    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(test[idx]), tol=1e-12)
+    for r, k in enumerate(idx):
+        assert np.abs(s[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() < 1e-6
+    net.close()
