@@ -336,6 +336,34 @@ def run_gpu(args):
         st["note"] = "O(N) scan form of the power step (Eq. 6 triangular structure); same pmfs, not the dense-path number"
         extra["structured"] = st
 
+    # uneven workload: 4096 pixels, N in {500..16000}, one persistent launch
+    if not args.no_uneven and rank == 0:
+        ux = W.uneven()
+        ucp = spl.pixels_to_c(ux)
+        uoff = spl.offsets_of(ux)
+        uout = torch.empty(int(uoff[-1]), dtype=torch.float32, device=dev)
+        udo = torch.from_numpy(uoff).to(dev)
+        un = {}
+        for name, pk in (("dense", spl.SPL_PASS_DENSE), ("structured", spl.SPL_PASS_STRUCTURED)):
+            _, _, ur = spl.batch_stationary(ux, tol=TOL, max_iter=MAX_ITER, out=uout, offsets=udo, c_pixels=ucp,
+                                            pass_kind=pk)
+            assert np.all(ur["status"] == 0)
+            fn = (lambda pk=pk: spl.batch_stationary(ux, tol=TOL, max_iter=MAX_ITER, out=uout, offsets=udo,
+                                                     c_pixels=ucp, reports=False, time_kernel=True, pass_kind=pk))
+            fn()
+            ums, ukern = timed_steps(fn, max(2, args.steps // 2), flush, stream, spl.batch_kernel_ms)
+            item = {"value": len(ux) / (statistics.mean(ums) / 1e3), "ms_per_step": statistics.mean(ums),
+                    "kernel_ms": statistics.median(ukern), "iters_mean": float(ur["iters"].mean()),
+                    "iters_max": int(ur["iters"].max())}
+            if pk == spl.SPL_PASS_DENSE:
+                uf = float(2.0 * np.sum(ux["n_bins"].astype(np.float64) ** 2 * (1 + ur["iters"])))
+                ua = uf / (item["kernel_ms"] / 1e3) / 1e12
+                item["roofline"] = {"bound": "alu", "achieved": ua, "peak": peak, "unit": "TFLOP/s", "frac": ua / peak}
+            un[name] = item
+        un["workload"] = "uneven: 4096 pixels, N~U{500,...,16000}, t_d~U[20,150], tau=30, sigma=0.3, B=0.5, S~U{0.05,0.5,5}, seed 4"
+        extra["uneven_4096"] = un
+        del uout
+
     # materialised vs matrix-free power step on one N = 10000 pixel (400 MB P)
     if not args.no_highres and rank == 0:
         hp = W.pixel(10000, 75.0, 30.0, 0.3, 0.5, 0.5)
@@ -424,6 +452,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
     ap.add_argument("--no-highres", action="store_true")
     ap.add_argument("--no-structured", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--train-pixels", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()

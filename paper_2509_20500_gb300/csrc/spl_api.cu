@@ -538,15 +538,14 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                        const int64_t *d_offsets,
                        cudaStream_t s, bool time_kernel = false, int structured = 0) {
     const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
-    if (threads != 256 && threads != 512 && threads != 1024) return SPL_EINVAL;
+    if (threads != 256 && threads != 512) return SPL_EINVAL;
     const int npad = batch_pad_len(nmax);
-    // Per-pixel state goes to shared memory when that still leaves room for
-    // several blocks per SM (up to ~3000 bins).
-    const bool state_smem = batch_smem_bytes(npad, true) <= 100 * 1024;
-    const size_t smem = batch_smem_bytes(npad, state_smem);
+    // Per-pixel vectors go to shared memory as far as three blocks per SM allow.
+    const int level = batch_state_level(npad);
+    const size_t smem = batch_smem_bytes(npad, level);
     if (smem > 220 * 1024) return SPL_EINVAL;
     int bps = 0;
-    SPL_CU(batch_occupancy(threads, smem, &bps));
+    SPL_CU(batch_occupancy(threads, level, smem, &bps));
     if (bps < 1) return SPL_EINVAL;
     int grid = bps * num_sms_current();
     if (grid > n) grid = n;
@@ -554,7 +553,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
     if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
     if ((e = grow(&ws.counter, &ws.counter_cap, 1)) != cudaSuccess) return status_of_alloc(e, "counter");
-    if (!state_smem && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * 5 * npad)) != cudaSuccess)
+    const size_t per_block = level == 2 ? 0 : (size_t)(level == 1 ? 5 : 7) * npad;
+    if (per_block && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * per_block)) != cudaSuccess)
         return status_of_alloc(e, "scratch");
     SPL_CU(cudaMemcpyAsync(ws.px, ws.h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
     SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
@@ -570,7 +570,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.reports = ws.reps;
     a.scratch = ws.scratch;
     a.npad_max = npad;
-    a.state_in_smem = state_smem ? 1 : 0;
+    a.state_level = level;
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);

@@ -324,12 +324,9 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
     u = lam_f / w;
 }
 
-template <int NT, int C>
+template <int NT, int C, int LEVEL>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fused_kernel(BatchArgs a) {
     extern __shared__ float4 smem4[];
-    float *sv = reinterpret_cast<float *>(smem4);
-    float *spi = sv + a.npad_max;
-    float *srho = spi + a.npad_max;
     __shared__ float red[8 * (NT / 32) + 8];
     __shared__ int s_item;
     __shared__ float s_scal[4];
@@ -337,17 +334,29 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
 
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    float *gw, *gu, *gy, *gd1, *gd2;
-    if (a.state_in_smem) {
-        gw = srho + a.npad_max;
-    } else {
-        gw = a.scratch + (size_t)blockIdx.x * 5 * a.npad_max;
-    }
-    gu = gw + a.npad_max;
-    gy = gu + a.npad_max;
-    gd1 = gy + a.npad_max;
-    gd2 = gd1 + a.npad_max;
-    double *s_thi = reinterpret_cast<double *>(a.state_in_smem ? (gd2 + a.npad_max) : (srho + a.npad_max));
+    // Per-pixel vectors: the broadcast vector v always lives in shared memory;
+    // level 2 keeps all eight vectors there, level 1 keeps v, pi, rho, level 0
+    // only v (the rest go to this block's slot of global scratch).  Addresses
+    // are formed where they are used (index 0 v, 1 pi, 2 rho, 3 w, 4 u, 5 y,
+    // 6 d1, 7 d2).
+    const int np = a.npad_max;
+    constexpr int level = LEVEL;
+    float *const smem_f = reinterpret_cast<float *>(smem4);
+    float *const gslot = LEVEL == 2 ? nullptr : a.scratch + (size_t)blockIdx.x * (LEVEL == 0 ? 7 : 5) * np;
+    auto vec = [&](int idx) -> float * {
+        if (LEVEL == 2 || idx == 0 || (LEVEL == 1 && idx <= 2)) return smem_f + (size_t)idx * np;
+        if (idx <= 2) return gslot + (size_t)(idx + 4) * np;
+        return gslot + (size_t)(idx - 3) * np;
+    };
+    float *sv = smem_f;
+#define spi (vec(1))
+#define srho (vec(2))
+#define gw (vec(3))
+#define gu (vec(4))
+#define gy (vec(5))
+#define gd1 (vec(6))
+#define gd2 (vec(7))
+    double *s_thi = reinterpret_cast<double *>(smem_f + (level == 2 ? 8 : (level == 1 ? 3 : 1)) * (size_t)np);
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -549,6 +558,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
         __syncthreads();
     }
 }
+
+#undef spi
+#undef srho
+#undef gw
+#undef gu
+#undef gy
+#undef gd1
+#undef gd2
 
 // ======================================================================
 // K1 for a single chain: per-bin vectors
@@ -985,49 +1002,62 @@ __global__ void __launch_bounds__(NT) finish_rows_kernel(int N, int nparts, int 
 // Launchers
 // ======================================================================
 
-int batch_threads_for(int nmax) { return nmax <= 4096 ? 256 : 1024; }
+int batch_threads_for(int nmax) { (void)nmax; return 256; }
 
-cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
-    if (threads == 512) {
-        auto k = batch_fused_kernel<512, SPL_BATCH_C>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, 512, smem, s>>>(a);
-    } else if (threads == 256) {
-        auto k = batch_fused_kernel<256, SPL_BATCH_C>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, 256, smem, s>>>(a);
-    } else {
-        auto k = batch_fused_kernel<1024, SPL_BATCH_C>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, 1024, smem, s>>>(a);
-    }
+template <int NT, int LEVEL>
+static cudaError_t launch_batch_one(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
+    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NT>
+cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
+    if (threads == 512) {
+        if (a.state_level == 2) return launch_batch_one<512, 2>(a, grid, smem, s);
+        if (a.state_level == 1) return launch_batch_one<512, 1>(a, grid, smem, s);
+        return launch_batch_one<512, 0>(a, grid, smem, s);
+    }
+    if (a.state_level == 2) return launch_batch_one<256, 2>(a, grid, smem, s);
+    if (a.state_level == 1) return launch_batch_one<256, 1>(a, grid, smem, s);
+    return launch_batch_one<256, 0>(a, grid, smem, s);
+}
+
+template <int NT, int LEVEL>
 static cudaError_t occupancy_one(size_t smem, int *bps) {
-    auto k = batch_fused_kernel<NT, SPL_BATCH_C>;
+    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, smem);
 }
 
-cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm) {
-    if (threads == 512) return occupancy_one<512>(smem, blocks_per_sm);
-    if (threads == 256) return occupancy_one<256>(smem, blocks_per_sm);
-    return occupancy_one<1024>(smem, blocks_per_sm);
+cudaError_t batch_occupancy(int threads, int level, size_t smem, int *blocks_per_sm) {
+    if (threads == 512) {
+        if (level == 2) return occupancy_one<512, 2>(smem, blocks_per_sm);
+        if (level == 1) return occupancy_one<512, 1>(smem, blocks_per_sm);
+        return occupancy_one<512, 0>(smem, blocks_per_sm);
+    }
+    if (level == 2) return occupancy_one<256, 2>(smem, blocks_per_sm);
+    if (level == 1) return occupancy_one<256, 1>(smem, blocks_per_sm);
+    return occupancy_one<256, 0>(smem, blocks_per_sm);
 }
 
 int batch_pad_len(int n) { return pad_len(n, SPL_BATCH_C); }
 
-// v, pi, rho (+ w, u, y, d1, d2 when in shared memory) and the FP64 table of
-// 64-bin blocks of the geometric flux factor.
-size_t batch_smem_bytes(int npad, bool state_in_smem) {
-    const size_t vec = (size_t)(state_in_smem ? 8 : 3) * npad * sizeof(float);
+// The vectors kept in shared memory at a state level (8, 3 or 1 of them) and
+// the FP64 table of 64-bin blocks of the geometric flux factor.
+size_t batch_smem_bytes(int npad, int level) {
+    const size_t vec = (size_t)(level == 2 ? 8 : (level == 1 ? 3 : 1)) * npad * sizeof(float);
     return vec + (size_t)(npad / 64 + 2) * sizeof(double);
+}
+
+// Largest state level whose shared memory still lets three 256-thread blocks
+// share an SM.
+int batch_state_level(int npad) {
+    if (batch_smem_bytes(npad, 2) <= 100 * 1024) return 2;
+    if (batch_smem_bytes(npad, 1) <= 72 * 1024) return 1;
+    return 0;
 }
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal, int npad,

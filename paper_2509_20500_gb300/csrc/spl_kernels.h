@@ -30,9 +30,9 @@ struct BatchArgs {
     float *out;              // packed output
     const int64_t *offsets;  // [n + 1] caller offsets by caller index, or NULL (use px.out_off)
     ReportDev *reports;      // [n] by caller index, may be NULL
-    float *scratch;          // [grid][5][npad_max] when the state is not in shared memory
+    float *scratch;          // [grid][5 or 7][npad_max] for the vectors not in shared memory
     int npad_max;
-    int state_in_smem;       // 1: w, u, y, d1, d2 in shared memory after v, pi, rho
+    int state_level;         // 2: all vectors in shared memory; 1: v, pi, rho; 0: v only
     float tol_err;
     int max_iter;
     int min_iter;
@@ -79,9 +79,10 @@ struct FinishArgs {
 };
 
 int batch_threads_for(int nmax);
-size_t batch_smem_bytes(int npad, bool state_in_smem);
+size_t batch_smem_bytes(int npad, int level);
+int batch_state_level(int npad);
 int batch_pad_len(int n);
-cudaError_t batch_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t batch_occupancy(int threads, int level, size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal,

@@ -155,10 +155,10 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
 
     const int threads = batch_threads_for(nmax);
     const int npad = batch_pad_len(nmax);
-    if (batch_smem_bytes(npad, true) > 100 * 1024) return SPL_EINVAL;
-    const size_t smem = batch_smem_bytes(npad, true);
+    if (batch_state_level(npad) != 2) return SPL_EINVAL;
+    const size_t smem = batch_smem_bytes(npad, 2);
     int bps = 0;
-    cudaError_t e = batch_occupancy(threads, smem, &bps);
+    cudaError_t e = batch_occupancy(threads, 2, smem, &bps);
     if (e != cudaSuccess || bps < 1) return SPL_ECUDA;
     int grid = bps * sm_count();
     if (grid > n) grid = n;
@@ -181,7 +181,7 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     a.reports = d_reps;
     a.scratch = nullptr;          // per-pixel state stays in shared memory at these sizes
     a.npad_max = npad;
-    a.state_in_smem = 1;
+    a.state_level = 2;
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = 1;

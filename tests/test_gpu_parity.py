@@ -316,3 +316,32 @@ def test_structured_and_dense_steps_agree_on_ragged_batch(spl):
         if p["n_bins"] <= 2000:
             ref = oracle.stationary(p, shift=oracle.shift_l(p))
             assert _l1(s[off[k]:off[k + 1]], ref) < L1_TOL, (k, p)
+
+
+def test_uneven_workload_full_batch(spl):
+    """The uneven workload (4096 pixels, N from 500 to 16000, t_d ~ U[20,150],
+    non-integer shifts) in one persistent launch; sampled pixels, including
+    the largest size, against the oracle with the same shift l."""
+    px = W.uneven()
+    out, off, reps = spl.batch_stationary(px, tol=1e-6)
+    assert np.all(reps["status"] == 0)
+    o = out.cpu().numpy()
+    Ns = px["n_bins"]
+    rng = np.random.default_rng(20)
+    pick = list(rng.choice(np.nonzero(Ns <= 2000)[0], 8, replace=False))
+    pick += list(rng.choice(np.nonzero(Ns == 8000)[0], 1)) + list(rng.choice(np.nonzero(Ns == 16000)[0], 1))
+    pix = W.as_dicts(px[pick])
+    for p in pix:
+        p["shift_override"] = oracle.shift_l(p)
+    refs = []
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(4) as ex:
+        refs = list(ex.map(lambda p: oracle.stationary(p, shift=p["shift_override"]), pix))
+    for k, ref in zip(pick, refs):
+        assert _l1(o[off[k]:off[k + 1]], ref) < L1_TOL, (k, int(Ns[k]))
+    # structured form on the same launch shape
+    s, _, rs = spl.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_STRUCTURED)
+    assert np.all(rs["status"] == 0)
+    s = s.cpu().numpy()
+    for k in pick:
+        assert _l1(s[off[k]:off[k + 1]], o[off[k]:off[k + 1]]) < 2 * L1_TOL
