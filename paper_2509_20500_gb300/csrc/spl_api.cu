@@ -541,11 +541,11 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     if (threads != 256 && threads != 512) return SPL_EINVAL;
     const int npad = batch_pad_len(nmax);
     // Per-pixel vectors go to shared memory as far as three blocks per SM allow.
-    const int level = batch_state_level(npad);
+    const int level = batch_state_level(npad, structured != 0);
     const size_t smem = batch_smem_bytes(npad, level);
     if (smem > 220 * 1024) return SPL_EINVAL;
     int bps = 0;
-    SPL_CU(batch_occupancy(threads, level, smem, &bps));
+    SPL_CU(batch_occupancy(threads, level, structured != 0, smem, &bps));
     if (bps < 1) return SPL_EINVAL;
     int grid = bps * num_sms_current();
     if (grid > n) grid = n;

@@ -181,8 +181,13 @@ struct StopState {
 };
 
 // Steps above this L1 size are far above the FP32 rounding noise of an
-// iterate (~1e-7), so the recurrence fit on them is trustworthy.
+// iterate (about 1e-7 to 4e-7), so a recurrence fit whose basis step
+// d_{k-1} is above it is trustworthy.  A reliable fit is only replaced by a
+// fit whose newest step is also above kRefitFloor (about 100x the noise): a
+// fit on a step a few tens of times the noise can lock onto the rounding
+// pattern instead of lambda_2.
 constexpr float kFitFloor = 3e-6f;
+constexpr float kRefitFloor = 1e-5f;
 // Modulus assumed for lambda_2 while no trustworthy fit exists (a start that
 // is already within noise of pi).  Over S, B in [0.01, 10] and t_d in
 // [20, 150] (t_r = 100) the largest |lambda_2| is about 0.87.
@@ -190,11 +195,12 @@ constexpr float kRhoDefault = 0.9f;
 // Below this L1 step the step-to-step ratio is dominated by rounding noise
 // and is not used to raise the modulus estimate.
 constexpr float kRatioFloor = 1e-6f;
-// Below this L1 step a step envelope that has stopped shrinking (the last
-// two steps at least 0.95 of the two before, slower than any |lambda_2| <=
-// 0.97 allows) marks the FP32 rounding floor of the map (about one unit in
-// the last place per element, ~1e-7 in L1): further steps cannot reduce
-// the error.
+// Rounding floor of the map: once the smallest of the last two steps no
+// longer falls below a fraction of the smallest of the two before (the
+// fraction a decay at the estimated |lambda_2| would give, at least 1/2),
+// while the step is below these sizes, the iterate sits on the FP32 floor
+// and further steps cannot reduce the error.
+constexpr float kStallFloorReliable = 1e-6f;
 constexpr float kStallFloor = 3e-7f;
 
 __host__ __device__ __forceinline__ void stop_init(StopState &s) {
@@ -248,7 +254,8 @@ __host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, 
     const int k = s.k;
     s.delta[(k - 1) & 7] = delta;
     if (k >= 3) {
-        const bool trusted = delta > kFitFloor;
+        const float basis = s.delta[(k - 2) & 7];
+        const bool trusted = s.reliable ? (delta > kRefitFloor) : (basis > kFitFloor);
         if (trusted || !s.reliable) {
             float r, th;
             if (fit_lambda2(s.g11, s.g12, s.g22, d1, d2, r, th)) {
@@ -286,10 +293,11 @@ __host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, 
     s.err = env * ru / (1.f - ru);
     if (delta == 0.f) s.err = 0.f;   // exact FP32 fixed point
     bool stalled = false;
-    if (k >= 4 && delta < kStallFloor) {
-        const float e_now = fmaxf(delta, prev);
-        const float e_old = fmaxf(s.delta[(k - 3) & 7], s.delta[(k - 4) & 7]);
-        stalled = e_now >= 0.95f * e_old;
+    if (k >= 5 && delta < (s.reliable ? kStallFloorReliable : kStallFloor)) {
+        const float lo_now = fminf(delta, prev);
+        const float lo_old = fminf(s.delta[(k - 3) & 7], s.delta[(k - 4) & 7]);
+        const float thr = s.reliable ? fmaxf(0.5f, fminf(0.95f, 4.f * s.rho * s.rho)) : 0.5f;
+        stalled = lo_now >= thr * lo_old;
     }
     return k >= min_iter && (s.err < tol_err || stalled);
 }

@@ -41,10 +41,15 @@ namespace spl {
 #define SPL_NCH 4
 #endif
 #ifndef SPL_BATCH_C
-#define SPL_BATCH_C 4
+#define SPL_BATCH_C 8
 #endif
 #ifndef SPL_BATCH_MINB
-#define SPL_BATCH_MINB 3
+#define SPL_BATCH_MINB 2
+#endif
+// 1: issue the four FFMA chains of a column as two packed FP32x2 FMAs
+// (fma.rn.f32x2, sm_100+), same per-lane rounding, half the instructions.
+#ifndef SPL_FFMA2
+#define SPL_FFMA2 1
 #endif
 constexpr int kChain = SPL_KCHAIN;
 constexpr int kNch = SPL_NCH;
@@ -88,6 +93,31 @@ template <int C>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
                                         float (&acc)[C], float (&comp)[C]) {
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
+#if SPL_FFMA2
+    static_assert(kNch == 4, "packed form keeps four chains per output");
+    float2 mm[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) mm[c] = make_float2(m[c], m[c]);
+    for (int b0 = lo; b0 < hi; b0 += kChain) {
+        const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
+        float2 in01[C], in23[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) { in01[c] = make_float2(0.f, 0.f); in23[c] = make_float2(0.f, 0.f); }
+#pragma unroll 8
+        for (int q = 0; q < q1; ++q) {
+            const float4 x = v4[(b0 >> 2) + q];
+            const float2 xa = make_float2(x.x, x.y), xb = make_float2(x.z, x.w);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                in01[c] = __ffma2_rn(xa, mm[c], in01[c]);
+                in23[c] = __ffma2_rn(xb, mm[c], in23[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            two_sum_acc(acc[c], comp[c], (in01[c].x + in01[c].y) + (in23[c].x + in23[c].y));
+    }
+#else
     for (int b0 = lo; b0 < hi; b0 += kChain) {
         const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
         float in[kNch][C];
@@ -105,6 +135,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         }
         chains_flush<C>(in, acc, comp);
     }
+#endif
 }
 
 // Column pass: out_c = sum_b v_b * (b <= a_c ? mlo_c : mhi_c)
@@ -324,8 +355,15 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
     u = lam_f / w;
 }
 
-template <int NT, int C, int LEVEL>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fused_kernel(BatchArgs a) {
+// Blocks per SM of the structured instantiation (no dense loops, few registers).
+#ifndef SPL_STRUCT_MINB
+#define SPL_STRUCT_MINB 6
+#endif
+constexpr int kStructMinBlocks = SPL_STRUCT_MINB;
+
+template <int NT, int C, int LEVEL, bool STRUCT>
+__global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? SPL_BATCH_MINB : 1))
+    batch_fused_kernel(BatchArgs a) {
     extern __shared__ float4 smem4[];
     __shared__ float red[8 * (NT / 32) + 8];
     __shared__ int s_item;
@@ -388,7 +426,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
         __syncthreads();
 
         // ---- row sums r'_k, rho_k = u_k / r'_k
-        if (a.structured) {
+        if constexpr (STRUCT) {
             // r'_k / u_k = sum_{j >= k} w_j + eL sum_{j < k} w_j: an inclusive
             // suffix scan and an inclusive prefix scan of w (prefix - w_k is the
             // exclusive prefix, whose rounding is damped by eL).
@@ -491,7 +529,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? SPL_BATCH_MINB : 1)) batch_fu
             }
             __syncthreads();
             float ysum = 0.f;
-            if (a.structured) {
+            if constexpr (STRUCT) {
                 // y_j = w_j (P_j + eL (T - P_j)), P = inclusive prefix of h, T = sum h
                 const float T = block_scan<NT>(sv, gy, N, false, red);
                 for (int j = tid; j < N; j += NT) {
@@ -1004,43 +1042,47 @@ __global__ void __launch_bounds__(NT) finish_rows_kernel(int N, int nparts, int 
 
 int batch_threads_for(int nmax) { (void)nmax; return 256; }
 
-template <int NT, int LEVEL>
+template <int NT, int LEVEL, bool STRUCT>
 static cudaError_t launch_batch_one(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
-    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL>;
+    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL, STRUCT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
-    if (threads == 512) {
-        if (a.state_level == 2) return launch_batch_one<512, 2>(a, grid, smem, s);
-        if (a.state_level == 1) return launch_batch_one<512, 1>(a, grid, smem, s);
-        return launch_batch_one<512, 0>(a, grid, smem, s);
-    }
-    if (a.state_level == 2) return launch_batch_one<256, 2>(a, grid, smem, s);
-    if (a.state_level == 1) return launch_batch_one<256, 1>(a, grid, smem, s);
-    return launch_batch_one<256, 0>(a, grid, smem, s);
+template <int NT, bool STRUCT>
+static cudaError_t launch_batch_nt(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
+    if (a.state_level == 2) return launch_batch_one<NT, 2, STRUCT>(a, grid, smem, s);
+    if (a.state_level == 1) return launch_batch_one<NT, 1, STRUCT>(a, grid, smem, s);
+    return launch_batch_one<NT, 0, STRUCT>(a, grid, smem, s);
 }
 
-template <int NT, int LEVEL>
+cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
+    if (a.structured) return launch_batch_nt<256, true>(a, grid, smem, s);
+    if (threads == 512) return launch_batch_nt<512, false>(a, grid, smem, s);
+    return launch_batch_nt<256, false>(a, grid, smem, s);
+}
+
+template <int NT, int LEVEL, bool STRUCT>
 static cudaError_t occupancy_one(size_t smem, int *bps) {
-    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL>;
+    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL, STRUCT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, smem);
 }
 
-cudaError_t batch_occupancy(int threads, int level, size_t smem, int *blocks_per_sm) {
-    if (threads == 512) {
-        if (level == 2) return occupancy_one<512, 2>(smem, blocks_per_sm);
-        if (level == 1) return occupancy_one<512, 1>(smem, blocks_per_sm);
-        return occupancy_one<512, 0>(smem, blocks_per_sm);
-    }
-    if (level == 2) return occupancy_one<256, 2>(smem, blocks_per_sm);
-    if (level == 1) return occupancy_one<256, 1>(smem, blocks_per_sm);
-    return occupancy_one<256, 0>(smem, blocks_per_sm);
+template <int NT, bool STRUCT>
+static cudaError_t occupancy_nt(int level, size_t smem, int *bps) {
+    if (level == 2) return occupancy_one<NT, 2, STRUCT>(smem, bps);
+    if (level == 1) return occupancy_one<NT, 1, STRUCT>(smem, bps);
+    return occupancy_one<NT, 0, STRUCT>(smem, bps);
+}
+
+cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm) {
+    if (structured) return occupancy_nt<256, true>(level, smem, blocks_per_sm);
+    if (threads == 512) return occupancy_nt<512, false>(level, smem, blocks_per_sm);
+    return occupancy_nt<256, false>(level, smem, blocks_per_sm);
 }
 
 int batch_pad_len(int n) { return pad_len(n, SPL_BATCH_C); }
@@ -1054,9 +1096,9 @@ size_t batch_smem_bytes(int npad, int level) {
 
 // Largest state level whose shared memory still lets three 256-thread blocks
 // share an SM.
-int batch_state_level(int npad) {
-    if (batch_smem_bytes(npad, 2) <= 100 * 1024) return 2;
-    if (batch_smem_bytes(npad, 1) <= 72 * 1024) return 1;
+int batch_state_level(int npad, bool structured) {
+    if (!structured && batch_smem_bytes(npad, 2) <= 100 * 1024) return 2;
+    if (batch_smem_bytes(npad, 1) <= (structured ? 48 : 72) * 1024) return 1;
     return 0;
 }
 

@@ -80,9 +80,9 @@ struct FinishArgs {
 
 int batch_threads_for(int nmax);
 size_t batch_smem_bytes(int npad, int level);
-int batch_state_level(int npad);
+int batch_state_level(int npad, bool structured);
 int batch_pad_len(int n);
-cudaError_t batch_occupancy(int threads, int level, size_t smem, int *blocks_per_sm);
+cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal,

@@ -155,10 +155,10 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
 
     const int threads = batch_threads_for(nmax);
     const int npad = batch_pad_len(nmax);
-    if (batch_state_level(npad) != 2) return SPL_EINVAL;
+    if (batch_state_level(npad, false) != 2) return SPL_EINVAL;
     const size_t smem = batch_smem_bytes(npad, 2);
     int bps = 0;
-    cudaError_t e = batch_occupancy(threads, 2, smem, &bps);
+    cudaError_t e = batch_occupancy(threads, 2, false, smem, &bps);
     if (e != cudaSuccess || bps < 1) return SPL_ECUDA;
     int grid = bps * sm_count();
     if (grid > n) grid = n;
