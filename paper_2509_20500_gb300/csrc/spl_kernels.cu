@@ -796,8 +796,10 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_tma_kernel(const __grid_con
         for (int it = 0; it < STAGES && it < ntiles; ++it) issue(it);
     }
     if (kSmemC) {
+        // stage the coefficients with many independent loads in flight
         const int rows = a.tiles_per_slab * kGemvRows;
-        for (int i = tid; i < rows; i += kGemvThreads) cs[i] = (i < a.N) ? a.c[i] : 0.f;
+#pragma unroll 8
+        for (int i = tid; i < rows; i += kGemvThreads) cs[i] = (i < a.N) ? __ldg(a.c + i) : 0.f;
         __syncthreads();
     }
     const int slab0 = t0 / a.tiles_per_slab;
