@@ -263,6 +263,12 @@ SPL_API spl_status_t spl_matrix(spl_chain_t *c, float *d_P);
  * events on the chain's stream.  Leaves the chain's iterate reset. */
 SPL_API spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass);
 
+/* Measurement: device time of the materialised build (the write of P and its
+ * row sums, Eq. 6 with the roll in the row address), averaged over `reps`
+ * rebuilds after one warm-up; the stored P is rewritten with the same
+ * values.  SPL_EINVAL for fused chains. */
+SPL_API spl_status_t spl_chain_time_build(spl_chain_t *c, int32_t reps, float *ms_per_build);
+
 /* Per-bin vectors of a built chain, for inspection: d_lambda (FP32 lambda(s_j)),
  * d_F (FP64 F(s_j)); either may be NULL.  h_Lambda (host, may be NULL) gets
  * Lambda; h_shift (may be NULL) the row shift in use. */

@@ -408,6 +408,28 @@ extern "C" spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float 
     return SPL_OK;
 }
 
+extern "C" spl_status_t spl_chain_time_build(spl_chain_t *c, int32_t reps, float *ms_per_build) {
+    if (!c || reps < 1 || !ms_per_build || c->mode != SPL_MATERIALIZED) return SPL_EINVAL;
+    cudaStream_t s = c->stream;
+    cudaEvent_t e0, e1;
+    SPL_CU(cudaEventCreate(&e0));
+    SPL_CU(cudaEventCreate(&e1));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < reps + 1 && e == cudaSuccess; ++i) {
+        if (i == 1) cudaEventRecord(e0, s);   // first build is a warm-up
+        e = launch_build_matrix(c->N, c->p.l, c->ld, c->w, c->u, c->scal, c->P, c->rowsum, num_sms_current(), s);
+    }
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "build timing");
+    *ms_per_build = ms / reps;
+    return SPL_OK;
+}
+
 extern "C" spl_status_t spl_matrix(spl_chain_t *c, float *d_P) {
     if (!c || !d_P || c->mode != SPL_MATERIALIZED) return SPL_EINVAL;
     SPL_CU(cudaMemcpy2DAsync(d_P, sizeof(float) * c->N, c->P, sizeof(float) * c->ld, sizeof(float) * c->N, c->N,

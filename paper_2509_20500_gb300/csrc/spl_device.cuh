@@ -160,6 +160,46 @@ __device__ __forceinline__ void block_sum_k(float (&v)[K], float *red /* >= K * 
     for (int k = 0; k < K; ++k) v[k] = red[K * NW + k];
 }
 
+// One-barrier block reductions: each warp reduces in registers, lane 0
+// publishes its partial in buf, one barrier, then every thread adds the
+// partials in the same order (identical results in all threads).  The
+// caller alternates buffers between consecutive reductions so a buffer is
+// never rewritten before every thread has read it.
+template <int NT>
+__device__ __forceinline__ float block_sum_1bar(float v, float *buf /* NT/32 */) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) buf[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += buf[w];
+    return t;
+}
+
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_k_1bar(float (&v)[K], float *buf /* K * NT/32 */) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) buf[k * NW + (threadIdx.x >> 5)] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += buf[k * NW + w];
+        v[k] = t;
+    }
+}
+
 // ---------------------------------------------------------------- stop rule
 
 // Convergence state of one pixel's power iteration.  The error of the

@@ -516,22 +516,29 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         StopState st;
         stop_init(st);
         int status = ST_ENOCONV;
-        for (int it = 0; it < a.max_iter; ++it) {
-            // h_k = pi_{(k - l) mod N} * rho_k  (J_l folded into the index)
-            for (int k = tid; k < npad; k += NT) {
-                float h = 0.f;
-                if (k < N) {
-                    int i = k - l;
-                    i += (i < 0) ? N : 0;
-                    h = spi[i] * srho[k];
-                }
-                sv[k] = h;
+        // h_k = pi_{(k - l) mod N} * rho_k (J_l folded into the index) for the
+        // first step; later steps get h from the statistics loop.
+        for (int k = tid; k < npad; k += NT) {
+            float h = 0.f;
+            if (k < N) {
+                int i = k - l;
+                i += (i < 0) ? N : 0;
+                h = spi[i] * srho[k];
             }
-            __syncthreads();
+            sv[k] = h;
+        }
+        __syncthreads();
+        // reduction scratch: [0, NW) step sums, [NW, 5 NW) step statistics,
+        // [6 NW, 8 NW + 2) the structured step's scan; disjoint, so no buffer is
+        // rewritten before every thread has read it
+        float *redA = red;
+        float *redS = red + NW;
+        float *redC = red + 6 * NW;
+        for (int it = 0; it < a.max_iter; ++it) {
             float ysum = 0.f;
             if constexpr (STRUCT) {
                 // y_j = w_j (P_j + eL (T - P_j)), P = inclusive prefix of h, T = sum h
-                const float T = block_scan<NT>(sv, gy, N, false, red);
+                const float T = block_scan<NT>(sv, gy, N, false, redC);
                 for (int j = tid; j < N; j += NT) {
                     const float P = gy[j];
                     const float y = gw[j] * fmaf(eL, T - P, P);
@@ -559,7 +566,8 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                 }
             }
             }
-            const float s = block_sum<NT>(ysum, red);   // also orders the y writes before the reads
+            // one barrier: orders the y writes and ends every read of h
+            const float s = block_sum_1bar<NT>(ysum, redA);
             const float inv = 1.f / s;
             float stats[4] = {0.f, 0.f, 0.f, 0.f};
             for (int j = tid; j < N; j += NT) {
@@ -573,8 +581,13 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                 gd2[j] = e1;
                 gd1[j] = d;
                 spi[j] = pn;
+                // next step's broadcast vector: h at k = (j + l) mod N
+                int k = j + l;
+                k -= (k >= N) ? N : 0;
+                sv[k] = pn * srho[k];
             }
-            block_sum_k<NT, 4>(stats, red);
+            // one barrier: orders pi, d and h before the next step
+            block_sum_k_1bar<NT, 4>(stats, redS);
             if (stop_update(st, stats[0], stats[1], stats[2], stats[3], a.tol_err, a.min_iter)) {
                 status = ST_OK;
                 break;

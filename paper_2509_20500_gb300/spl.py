@@ -53,7 +53,8 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
-            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass"]
+            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
+            "spl_chain_time_build"]
 
 _lib = None
 _lock = threading.Lock()
@@ -132,6 +133,8 @@ def lib():
         L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp,
                                                    ctypes.POINTER(spl_batch_opts_t)]
         L.spl_batch_stationary_learned.restype = ctypes.c_int
+        L.spl_chain_time_build.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
+        L.spl_chain_time_build.restype = ctypes.c_int
         L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.spl_chain_time_pass.restype = ctypes.c_int
         L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
@@ -206,6 +209,12 @@ class Chain:
         """Device ms of one dense power-step pass (spl_chain_time_pass)."""
         ms = ctypes.c_float()
         _check(lib().spl_chain_time_pass(self._c, int(reps), ctypes.byref(ms)), "spl_chain_time_pass")
+        return float(ms.value)
+
+    def time_build(self, reps: int = 10) -> float:
+        """Device ms of one materialised build (spl_chain_time_build)."""
+        ms = ctypes.c_float()
+        _check(lib().spl_chain_time_build(self._c, int(reps), ctypes.byref(ms)), "spl_chain_time_build")
         return float(ms.value)
 
     def matrix(self):
