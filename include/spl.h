@@ -162,6 +162,21 @@ SPL_API spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int32_
                                      const float *d_warm, float *d_out, const int64_t *d_offsets,
                                      spl_report_t *h_reports, void *stream, const spl_batch_opts_t *opts);
 
+/*
+ * Spectral analysis of many pixels (Sec. 4, Fig. 4 columns 1-2): the modulus
+ * and phase of lambda_2, the subdominant eigenvalue of P~ that sets the
+ * spectral gap 1 - |lambda_2| and the oscillation of the convergence.
+ * Per pixel: pi by power iteration, then `subspace_iters` steps of
+ * orthogonal iteration on two vectors deflated against pi with a 2 x 2
+ * Rayleigh-Ritz projection (complex pairs resolved); every product with P~
+ * uses the O(N) structured form of Eq. 6.  FP32; accuracy about 1e-4 when
+ * |lambda_3| / |lambda_2| is well below 1.
+ *   d_out : device [n][2] floats: |lambda_2|, |arg lambda_2| in [0, pi].
+ * n_bins <= 4096.  Synchronises `stream`.
+ */
+SPL_API spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t n, int32_t subspace_iters,
+                                        float *d_out, void *stream);
+
 /* Device time in ms of the batch kernel of the last spl_batch_stationary_ex
  * call on the current device that set time_kernel (events recorded on that
  * call's stream just before and after the kernel launch).  Waits for the end

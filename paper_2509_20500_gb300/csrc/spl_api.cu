@@ -702,6 +702,35 @@ extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, i
     return SPL_OK;
 }
 
+extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t n, int32_t subspace_iters,
+                                           float *d_out, void *stream) {
+    if (n < 0 || (n > 0 && (!h_pixels || !d_out)) || subspace_iters < 1) return SPL_EINVAL;
+    if (n == 0) return SPL_OK;
+    BatchWorkspace *ws = nullptr;
+    spl_status_t st = ws_get(&ws);
+    if (st != SPL_OK) return st;
+    std::lock_guard<std::mutex> lock(ws->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int nmax = 0;
+    st = make_work_list(*ws, h_pixels, n, &nmax);
+    if (st != SPL_OK) return st;
+    if (nmax > 4096) return SPL_EINVAL;
+    cudaError_t e;
+    if ((e = grow(&ws->px, &ws->px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
+    SPL_CU(cudaMemcpyAsync(ws->px, ws->h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
+    SpectralArgs a{};
+    a.px = ws->px;
+    a.n = n;
+    a.npad_max = batch_pad_len(nmax);
+    a.pi_iters = 500;
+    a.subspace_iters = subspace_iters;
+    a.out = d_out;
+    const int grid = std::min(n, 2 * num_sms_current());
+    SPL_CU(launch_spectral(a, grid, s));
+    SPL_CU(cudaStreamSynchronize(s));   // the pinned work list is reused by the next call
+    return SPL_OK;
+}
+
 extern "C" spl_status_t spl_batch_kernel_ms(float *ms) {
     if (!ms) return SPL_EINVAL;
     BatchWorkspace *ws = nullptr;

@@ -618,6 +618,186 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
 #undef gd1
 #undef gd2
 
+
+// ======================================================================
+// K8: spectral analysis (|lambda_2| and its phase, Sec. 4)
+// ======================================================================
+//
+// One block per pixel.  After the flux factors and row sums (structured
+// form), pi is found by power iteration, then the subdominant eigenvalues
+// of P~ by orthogonal iteration on two vectors deflated against pi:
+//   Y = X P~ - (X P~ 1) pi      (P~ 1 = 1, pi 1 = 1: removes the lambda = 1 part)
+//   H_ab = <y_a, x_b>           (2 x 2 projection; its eigenvalues tend to the
+//                                two largest-modulus eigenvalues below 1,
+//                                a complex pair or two real ones)
+//   X = orthonormalise(Y)
+// Every product x P~ uses the O(N) structured form of Eq. 6.  Results:
+// out[2k] = |lambda_2|, out[2k+1] = |arg lambda_2| of pixel k.
+
+// y = x P~ in the structured form (x indexed by row i, y by column j).
+template <int NT>
+__device__ __forceinline__ float apply_structured(const float *x, const float *rho, const float *w, float eL, int N,
+                                                  int l, float *hbuf, float *y, float *red) {
+    for (int k = threadIdx.x; k < N; k += NT) {
+        int i = k - l;
+        i += (i < 0) ? N : 0;
+        hbuf[k] = x[i] * rho[k];
+    }
+    __syncthreads();
+    const float T = block_scan<NT>(hbuf, y, N, false, red);
+    float sy = 0.f;
+    for (int j = threadIdx.x; j < N; j += NT) {
+        const float P = y[j];
+        const float v = w[j] * fmaf(eL, T - P, P);
+        y[j] = v;
+        sy += v;
+    }
+    return sy;   // per-thread partial sum of y
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs a) {
+    extern __shared__ float4 smem4[];
+    constexpr int NW = NT / 32;
+    // reduction scratch: two alternating buffers of 4 NW (one-barrier
+    // reductions never reuse the buffer of the reduction just before), and
+    // the scan's own region
+    __shared__ float red[10 * NW + 8];
+    __shared__ double s_tlo[64];
+    const int np = a.npad_max;
+    float *base = reinterpret_cast<float *>(smem4);
+    float *w = base, *rho = base + np, *pi = base + 2 * np, *x = base + 3 * np, *z = base + 4 * np;
+    float *y1 = base + 5 * np, *y2 = base + 6 * np, *hb = base + 7 * np;
+    double *s_thi = reinterpret_cast<double *>(base + 8 * (size_t)np);
+    float *redC = red + 8 * NW;
+    bool flip = false;
+    auto buf = [&]() -> float * { flip = !flip; return flip ? red : red + 4 * NW; };
+    const int tid = threadIdx.x;
+
+    for (int item = blockIdx.x; item < a.n; item += gridDim.x) {
+        const PixelDev p = a.px[item];
+        const int N = p.N, l = p.l;
+        BatchFlux bf;
+        batch_flux_setup(p, bf, s_tlo, s_thi, (N + 63) >> 6);
+        const float eL = (float)exp(-bf.Lambda);
+        __syncthreads();
+        for (int j = tid; j < N; j += NT) {
+            float wj, uj, lam;
+            batch_flux_bin(p, bf, s_tlo, s_thi, j, wj, uj, lam);
+            w[j] = wj;
+        }
+        __syncthreads();
+        block_scan<NT>(w, y1, N, false, redC);       // prefix
+        block_scan<NT>(w, y2, N, true, redC);        // suffix
+        for (int k = tid; k < N; k += NT) rho[k] = 1.f / (y2[k] + eL * (y1[k] - w[k]));
+        for (int j = tid; j < N; j += NT) pi[j] = 1.f / (float)N;
+        __syncthreads();
+        // pi by power iteration (structured step) to a small step
+        for (int it = 0; it < a.pi_iters; ++it) {
+            const float sy = block_sum_1bar<NT>(apply_structured<NT>(pi, rho, w, eL, N, l, hb, y1, redC), buf());
+            float dl = 0.f;
+            for (int j = tid; j < N; j += NT) {
+                const float pn = y1[j] / sy;
+                dl += fabsf(pn - pi[j]);
+                pi[j] = pn;
+            }
+            const float delta = block_sum_1bar<NT>(dl, buf());
+            if (delta < 1e-7f) break;
+        }
+        // deterministic start vectors (hashed from bin and pixel index)
+        for (int j = tid; j < N; j += NT) {
+            uint32_t hx = (uint32_t)j * 2654435761u ^ (uint32_t)(p.index + 1) * 2246822519u;
+            hx ^= hx >> 15;
+            hx *= 2246822519u;
+            hx ^= hx >> 13;
+            uint32_t hz = hx * 3266489917u + 374761393u;
+            hz ^= hz >> 16;
+            x[j] = (float)(hx & 0xFFFFFF) / 16777216.f - 0.5f;
+            z[j] = (float)(hz & 0xFFFFFF) / 16777216.f - 0.5f;
+        }
+        __syncthreads();
+        float H[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int m = 0; m <= a.subspace_iters; ++m) {
+            // (1) deflate against pi and orthonormalise x, z (Gram-Schmidt)
+            float sxz[2] = {0.f, 0.f};
+            for (int j = tid; j < N; j += NT) { sxz[0] += x[j]; sxz[1] += z[j]; }
+            block_sum_k_1bar<NT, 2>(sxz, buf());
+            float nx = 0.f;
+            for (int j = tid; j < N; j += NT) {
+                const float v = x[j] - sxz[0] * pi[j];
+                x[j] = v;
+                z[j] = z[j] - sxz[1] * pi[j];
+                nx = fmaf(v, v, nx);
+            }
+            nx = block_sum_1bar<NT>(nx, buf());
+            const float ix = nx > 0.f ? rsqrtf(nx) : 0.f;
+            float dxz = 0.f;
+            for (int j = tid; j < N; j += NT) {
+                x[j] *= ix;
+                dxz = fmaf(x[j], z[j], dxz);
+            }
+            dxz = block_sum_1bar<NT>(dxz, buf());
+            float nz = 0.f;
+            for (int j = tid; j < N; j += NT) {
+                const float v = z[j] - dxz * x[j];
+                z[j] = v;
+                nz = fmaf(v, v, nz);
+            }
+            nz = block_sum_1bar<NT>(nz, buf());
+            const float iz = nz > 0.f ? rsqrtf(nz) : 0.f;
+            for (int j = tid; j < N; j += NT) z[j] *= iz;
+            __syncthreads();
+            if (m == a.subspace_iters) break;
+            // (2) Y = X P~ deflated, (3) projection H_ab = <y_a, x_b>
+            const float s1 = block_sum_1bar<NT>(apply_structured<NT>(x, rho, w, eL, N, l, hb, y1, redC), buf());
+            const float s2 = block_sum_1bar<NT>(apply_structured<NT>(z, rho, w, eL, N, l, hb, y2, redC), buf());
+            float hh[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int j = tid; j < N; j += NT) {
+                const float a1 = y1[j] - s1 * pi[j], a2 = y2[j] - s2 * pi[j];
+                hh[0] = fmaf(a1, x[j], hh[0]);
+                hh[1] = fmaf(a1, z[j], hh[1]);
+                hh[2] = fmaf(a2, x[j], hh[2]);
+                hh[3] = fmaf(a2, z[j], hh[3]);
+                x[j] = a1;
+                z[j] = a2;
+            }
+            block_sum_k_1bar<NT, 4>(hh, buf());
+#pragma unroll
+            for (int q = 0; q < 4; ++q) H[q] = hh[q];
+        }
+        if (tid == 0) {
+            // eigenvalues of the projection (x -> H0 x + H1 z, z -> H2 x + H3 z)
+            const double tr = (double)H[0] + H[3];
+            const double det = (double)H[0] * H[3] - (double)H[1] * H[2];
+            const double disc = tr * tr - 4.0 * det;
+            double mod, ph;
+            if (disc < 0.0) {
+                mod = sqrt(fmax(det, 0.0));
+                ph = atan2(sqrt(-disc), tr);
+            } else {
+                const double r1 = 0.5 * (tr + sqrt(disc)), r2 = 0.5 * (tr - sqrt(disc));
+                const double r = fabs(r1) >= fabs(r2) ? r1 : r2;
+                mod = fabs(r);
+                ph = r >= 0.0 ? 0.0 : 3.14159265358979323846;
+            }
+            a.out[2 * (size_t)p.index] = (float)mod;
+            a.out[2 * (size_t)p.index + 1] = (float)ph;
+        }
+        __syncthreads();
+    }
+}
+
+size_t spectral_smem_bytes(int npad) { return (size_t)8 * npad * sizeof(float) + (size_t)(npad / 64 + 2) * 8; }
+
+cudaError_t launch_spectral(const SpectralArgs &a, int grid, cudaStream_t s) {
+    auto k = spectral_kernel<256>;
+    const size_t smem = spectral_smem_bytes(a.npad_max);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ======================================================================
 // K1 for a single chain: per-bin vectors
 // ======================================================================

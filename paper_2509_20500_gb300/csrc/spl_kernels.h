@@ -78,6 +78,18 @@ struct FinishArgs {
     ChainState *state;
 };
 
+struct SpectralArgs {
+    const PixelDev *px;      // work list (index = caller position)
+    int n;
+    int npad_max;
+    int pi_iters;            // power steps for pi (stops early at a 1e-7 step)
+    int subspace_iters;      // orthogonal-iteration steps
+    float *out;              // [n][2]: |lambda_2|, |arg lambda_2|
+};
+
+size_t spectral_smem_bytes(int npad);
+cudaError_t launch_spectral(const SpectralArgs &a, int grid, cudaStream_t s);
+
 int batch_threads_for(int nmax);
 size_t batch_smem_bytes(int npad, int level);
 int batch_state_level(int npad, bool structured);

@@ -54,7 +54,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
-            "spl_chain_time_build"]
+            "spl_chain_time_build", "spl_batch_spectral"]
 
 _lib = None
 _lock = threading.Lock()
@@ -133,6 +133,8 @@ def lib():
         L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp,
                                                    ctypes.POINTER(spl_batch_opts_t)]
         L.spl_batch_stationary_learned.restype = ctypes.c_int
+        L.spl_batch_spectral.argtypes = [ctypes.POINTER(spl_pixel_t), i32, i32, vp, vp]
+        L.spl_batch_spectral.restype = ctypes.c_int
         L.spl_chain_time_build.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.spl_chain_time_build.restype = ctypes.c_int
         L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
@@ -288,6 +290,16 @@ def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 
                                             _dptr(offsets), reps, _stream_ptr(stream))
     _check(st, "spl_batch_stationary_noalloc", (SPL_OK, SPL_ENOCONV))
     return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def batch_spectral(px: np.ndarray, subspace_iters: int = 60, stream=None):
+    """spl_batch_spectral: (|lambda_2|, |arg lambda_2|) per pixel as a [n, 2] CUDA tensor."""
+    import torch
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    out = torch.empty((max(1, len(px)), 2), dtype=torch.float32, device="cuda")
+    _check(lib().spl_batch_spectral(pixels_to_c(px), len(px), int(subspace_iters), _dptr(out), _stream_ptr(stream)),
+           "spl_batch_spectral")
+    return out[:len(px)]
 
 
 def batch_kernel_ms() -> float:

@@ -345,3 +345,42 @@ def test_uneven_workload_full_batch(spl):
     s = s.cpu().numpy()
     for k in pick:
         assert _l1(s[off[k]:off[k + 1]], o[off[k]:off[k + 1]]) < 2 * L1_TOL
+
+
+# ---------------------------------------------------------------- spectral analysis (Sec. 4)
+
+def test_spectral_kernel_vs_lapack(spl):
+    """|lambda_2| and its phase from the GPU orthogonal iteration against
+    LAPACK eigenvalues of the oracle's P~, over the S, B grid of Sec. 3.5 at
+    both dead times of Sec. 4.2 (complex pairs included)."""
+    rows = []
+    for t_d in (75.0, 95.0):
+        for S in (0.1, 3.0, 9.0):
+            for B in (0.1, 3.0, 9.0):
+                rows.append(W.pixel(256, t_d, 30.0, 0.5, S, B))
+    px = np.concatenate(rows)
+    got = spl.batch_spectral(px, subspace_iters=120).cpu().numpy()
+    for k, p in enumerate(W.as_dicts(px)):
+        Pt = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+        w = np.linalg.eigvals(Pt)
+        w = w[np.argsort(-np.abs(w))]
+        sep = abs(w[3] if abs(np.imag(w[1])) > 1e-9 else w[2]) / abs(w[1])
+        if sep > 0.9:
+            continue
+        assert abs(got[k, 0] - abs(w[1])) < 2e-3 * abs(w[1]) + 2e-4, (k, got[k], w[:4])
+        assert abs(got[k, 1] - abs(np.angle(w[1]))) < 2e-2, (k, got[k], w[:4])
+
+
+def test_spectral_statements_of_sec4_on_gpu(spl):
+    """The paper's observations hold for the GPU estimates: the gap shrinks
+    with B; at t_d = 75 the phase grows with B; at t_d = 95 strong signal
+    gives near-zero phase."""
+    Ss, Bs = (0.1, 1.0, 3.0, 6.0, 9.0), (0.1, 1.0, 3.0, 6.0, 9.0)
+    res = {}
+    for t_d in (75.0, 95.0):
+        px = np.concatenate([W.pixel(256, t_d, 30.0, 0.5, S, B) for S in Ss for B in Bs])
+        res[t_d] = spl.batch_spectral(px, subspace_iters=120).cpu().numpy().reshape(5, 5, 2)
+    for t_d in res:
+        assert np.all(np.diff(res[t_d][:, :, 0], axis=1) > 0)
+    assert np.all(np.diff(res[75.0][:, 1:, 1], axis=1) > 0)
+    assert np.all(res[95.0][3:, :, 1] < 0.2)

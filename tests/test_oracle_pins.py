@@ -250,3 +250,35 @@ def test_batch_matches_single():
     assert used == 3 and np.all(iters > 0)
     for k, p in enumerate(px):
         np.testing.assert_array_equal(out[off[k]:off[k + 1]], oracle.stationary(p))
+
+
+# ---------------------------------------------------------------- spectral statements of Sec. 4
+
+def _lambda2_grid(t_d, Ss=(0.1, 1.0, 3.0, 6.0, 9.0), Bs=(0.1, 1.0, 3.0, 6.0, 9.0), N=256):
+    mod = np.zeros((len(Ss), len(Bs)))
+    ph = np.zeros_like(mod)
+    for a, S in enumerate(Ss):
+        for b, B in enumerate(Bs):
+            p = _px(n_bins=N, t_d=t_d, S=S, B=B)
+            Pt = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+            w = np.linalg.eigvals(Pt)
+            w = w[np.argsort(-np.abs(w))]
+            mod[a, b], ph[a, b] = abs(w[1]), abs(np.angle(w[1]))
+    return mod, ph
+
+
+@pytest.mark.parametrize("t_d", [75.0, 95.0])
+def test_spectral_gap_decreases_with_background(t_d):
+    """Sec. 4.1: the gap 1 - |lambda_2| decreases as B increases."""
+    mod, _ = _lambda2_grid(t_d)
+    assert np.all(np.diff(mod, axis=1) > 0)
+
+
+def test_phase_of_lambda2_patterns():
+    """Sec. 4.2: at t_d = 75 the phase of lambda_2 grows with B; at t_d = 95 a
+    large region (strong signal) has near-zero phase."""
+    _, ph75 = _lambda2_grid(75.0)
+    _, ph95 = _lambda2_grid(95.0)
+    assert np.all(np.diff(ph75[:, 1:], axis=1) > 0)          # B >= 1
+    assert np.all(ph95[3:, :] < 0.2)                           # S >= 6
+    assert np.all(ph75[3:, 2:] > 0.5)                          # same region at t_d = 75 oscillates
