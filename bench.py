@@ -137,8 +137,9 @@ def batch_kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic():
-    """DRAM bytes per launch of the batch kernel from the last ncu capture
+def stored_traffic(arm: str):
+    """DRAM bytes per launch of the batch kernel on the 65536-pixel array for
+    the given arm ("plain" or "learned") from the last ncu capture
     (profiles/batch_fused_kernel_traffic.json), or None if the kernel source
     changed since."""
     try:
@@ -147,7 +148,10 @@ def stored_traffic():
         return None
     if d.get("source_hash") != batch_kernel_source_hash():
         return None
-    return float(d["dram_bytes_read_per_launch"]) + float(d["dram_bytes_write_per_launch"])
+    a = d.get("arms", {}).get(arm)
+    if a is None:
+        return None
+    return float(a["dram_bytes_read_per_launch"]) + float(a["dram_bytes_write_per_launch"])
 
 
 def measured_peaks():
@@ -314,10 +318,13 @@ def run_gpu(args):
     kms = statistics.median(kern_ms)
     achieved = flop / (kms / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = stored_traffic() if n == 65536 else None
+    arm = "learned" if learned else "plain"
+    traffic = stored_traffic(arm) if n == 65536 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "batch_fused_kernel", "kernel_ms": kms,
-            "algorithmic_bytes": float(total * 4 + n * 40),
+            "algorithmic_bytes": float(total * 4 * (2 if learned else 1) + n * 40),
+            "bytes_basis": "pmf write (4 B per bin)" + (" + learned logits read (4 B per bin)" if learned else "")
+                           + " + 40 B of parameters per pixel", "arm": arm,
             "work": "2 FLOP x N^2 x (1 + iters) per pixel (row pass + power steps, one FFMA per entry)",
             "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock), derived"}
     if clocks.get("sm_mhz"):

@@ -59,7 +59,8 @@ typedef enum {
     SPL_EINVAL = 1,    /* invalid argument: bad theta, NULL pointer, n < 0, size limit */
     SPL_ENOMEM = 2,    /* device or host allocation failed */
     SPL_ECUDA = 3,     /* a CUDA runtime/driver call failed */
-    SPL_ENOCONV = 4,   /* max_iter steps did not meet the stop rule; result is the last iterate */
+    SPL_ENOCONV = 4,   /* max_iter steps did not meet the stop rule, or the iterate settled on an FP32
+                          rounding floor above the tolerance; result is the last iterate */
     SPL_ETIMEOUT = 5,  /* a bounded device-side wait gave up; result undefined */
 } spl_status_t;
 

@@ -216,6 +216,7 @@ struct StopState {
     float g11, g12, g22;  // <d_{k-1},d_{k-1}>, <d_{k-1},d_{k-2}>, <d_{k-2},d_{k-2}>
     float rho, theta;     // current |lambda_2| and phase estimates (rho < 0: none yet)
     float err;            // last error bound
+    float bmin, bmin_prev;  // smallest step of the current and the previous 8-step block
     int32_t k;            // steps taken
     int32_t reliable;     // 1 once a fit was made on steps well above FP32 noise
 };
@@ -242,6 +243,20 @@ constexpr float kRatioFloor = 1e-6f;
 // and further steps cannot reduce the error.
 constexpr float kStallFloorReliable = 1e-6f;
 constexpr float kStallFloor = 3e-7f;
+// Long-window floor test.  A start already within noise of pi gives no step
+// large enough for a trustworthy fit, and its noise floor can sit just above
+// kStallFloor.  Over 8 steps a decay at |lambda_2| <= 0.9 shrinks the
+// smallest step of a block to at most 0.43 of the previous block's (to
+// rho^8 for a trusted estimate rho); steps below kRefitFloor whose block
+// minimum stays above kBlockStall (or rho^4) of the previous one are
+// rounding noise.  Below kStallFloorReliable the iterate is within the
+// tolerance; above it the FP32 floor is too high for the tolerance, and
+// further steps cannot help, so the iteration ends as not converged.
+constexpr int kBlock = 8;
+constexpr float kBlockStall = 0.7f;
+
+// Outcomes of stop_update.
+enum : int { STOP_CONTINUE = 0, STOP_CONVERGED = 1, STOP_FLOOR = 2 };
 
 __host__ __device__ __forceinline__ void stop_init(StopState &s) {
 #pragma unroll
@@ -250,6 +265,8 @@ __host__ __device__ __forceinline__ void stop_init(StopState &s) {
     s.rho = -1.f;
     s.theta = 0.f;
     s.err = INFINITY;
+    s.bmin = INFINITY;
+    s.bmin_prev = INFINITY;
     s.k = 0;
     s.reliable = 0;
 }
@@ -286,9 +303,11 @@ __host__ __device__ __forceinline__ bool fit_lambda2(float g11, float g12, float
 }
 
 // Consume one step's reductions: delta = ||d_k||_1, dd = <d_k,d_k>,
-// d1 = <d_k,d_{k-1}>, d2 = <d_k,d_{k-2}>.  Returns true when the bound on the
-// error of pi_k is below tol_err (and k >= min_iter).
-__host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, float dd, float d1, float d2,
+// d1 = <d_k,d_{k-1}>, d2 = <d_k,d_{k-2}>.  Returns STOP_CONVERGED when the
+// bound on the error of pi_k is below tol_err or the iterate sits on an FP32
+// floor below the tolerance, STOP_FLOOR when it sits on a floor above it
+// (both only once k >= min_iter), else STOP_CONTINUE.
+__host__ __device__ __forceinline__ int stop_update(StopState &s, float delta, float dd, float d1, float d2,
                                             float tol_err, int min_iter) {
     s.k += 1;
     const int k = s.k;
@@ -309,7 +328,18 @@ __host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, 
     s.g22 = s.g11;
     s.g12 = d1;
     s.g11 = dd;
-    if (k < 3) return false;
+    s.bmin = fminf(s.bmin, delta);
+    int floor_long = STOP_CONTINUE;
+    if (k % kBlock == 0) {
+        if (k >= 2 * kBlock && s.bmin < kRefitFloor) {
+            const float r2 = s.rho * s.rho;
+            const float thr = s.reliable ? fmaxf(kBlockStall, r2 * r2) : kBlockStall;
+            if (s.bmin >= thr * s.bmin_prev) floor_long = s.bmin < kStallFloorReliable ? STOP_CONVERGED : STOP_FLOOR;
+        }
+        s.bmin_prev = s.bmin;
+        s.bmin = INFINITY;
+    }
+    if (k < 3) return STOP_CONTINUE;
     float ru;
     int W = 2;
     const float prev = s.delta[(k - 2) & 7];
@@ -336,10 +366,14 @@ __host__ __device__ __forceinline__ bool stop_update(StopState &s, float delta, 
     if (k >= 5 && delta < (s.reliable ? kStallFloorReliable : kStallFloor)) {
         const float lo_now = fminf(delta, prev);
         const float lo_old = fminf(s.delta[(k - 3) & 7], s.delta[(k - 4) & 7]);
-        const float thr = s.reliable ? fmaxf(0.5f, fminf(0.95f, 4.f * s.rho * s.rho)) : 0.5f;
+        // the decay the latest fit predicts over two steps (an untrusted fit
+        // still tells a slow mode from noise when the mode dominates)
+        const float thr = s.rho >= 0.f ? fmaxf(0.5f, fminf(0.95f, 4.f * s.rho * s.rho)) : 0.5f;
         stalled = lo_now >= thr * lo_old;
     }
-    return k >= min_iter && (s.err < tol_err || stalled);
+    if (k < min_iter) return STOP_CONTINUE;
+    if (s.err < tol_err || stalled) return STOP_CONVERGED;
+    return floor_long;
 }
 
 // ---------------------------------------------------------------- bounded waits

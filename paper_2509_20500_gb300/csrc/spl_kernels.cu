@@ -588,8 +588,9 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
             }
             // one barrier: orders pi, d and h before the next step
             block_sum_k_1bar<NT, 4>(stats, redS);
-            if (stop_update(st, stats[0], stats[1], stats[2], stats[3], a.tol_err, a.min_iter)) {
-                status = ST_OK;
+            const int su = stop_update(st, stats[0], stats[1], stats[2], stats[3], a.tol_err, a.min_iter);
+            if (su != STOP_CONTINUE) {
+                status = su == STOP_CONVERGED ? ST_OK : ST_ENOCONV;
                 break;
             }
         }
@@ -1149,11 +1150,12 @@ __global__ void __launch_bounds__(NT) finish_step_kernel(FinishArgs a) {
     }
     block_sum_k<NT, 4>(stats, red);
     StopState st = stp->st;
-    const bool stop = stop_update(st, stats[0], stats[1], stats[2], stats[3], stp->tol_err, stp->min_iter);
+    const int su = stop_update(st, stats[0], stats[1], stats[2], stats[3], stp->tol_err, stp->min_iter);
+    const bool stop = su != STOP_CONTINUE;
     __syncthreads();
     if (tid == 0) {
         stp->st = st;
-        if (stop) { stp->done = 1; stp->status = ST_OK; }
+        if (stop) { stp->done = 1; stp->status = su == STOP_CONVERGED ? ST_OK : ST_ENOCONV; }
         else if (st.k >= stp->max_iter) { stp->done = 1; stp->status = ST_ENOCONV; }
     }
     if (stop) return;

@@ -1,0 +1,157 @@
+"""The power iteration's stop rule, compiled for the host and replayed on
+synthetic step sequences whose true error is known.
+
+The iterate is modelled as pi_k = pi + e_k + eta_k: e_k the transient of
+one or two modes (a real lambda_2, or a complex pair rho e^{+-i theta}, as
+Sec. 4 finds for P~) and eta_k a rounding term of fixed L1 size (fresh
+random vectors, or a two-state cycle, the FP32 fixed points the kernel
+meets).  Requirements: whenever the rule stops, the true L1 error
+||e_k + eta_k||_1 is below the parity tolerance 1e-6; a start already at
+the noise floor stops within two 8-step blocks; a clean transient stops
+within a few steps of the first one whose true error is below tol_err.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = 1e-6
+TOL_ERR = 0.5 * TOL
+M = 512
+
+
+@pytest.fixture(scope="module")
+def rule(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("stop") / "libstoprule.so")
+    subprocess.run([nvcc, "-shared", "-Xcompiler", "-fPIC", "-O2", "-std=c++17",
+                    "-gencode", "arch=compute_103a,code=sm_103a", "-o", out,
+                    os.path.join(HERE, "stop_rule_host.cu")], check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    f = lib.stop_rule_replay
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                  ctypes.POINTER(ctypes.c_int)]
+
+    def replay(d, min_iter=1):
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        err, rho, th, rel = ctypes.c_float(), ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+        k = f(d.ctypes.data, d.shape[0], d.shape[1], TOL_ERR, min_iter, ctypes.byref(err), ctypes.byref(rho),
+              ctypes.byref(th), ctypes.byref(rel))
+        return k, dict(err=err.value, rho=rho.value, theta=th.value, reliable=rel.value)
+    return replay
+
+
+def _zero_sum_unit(rng, n=1):
+    v = rng.standard_normal((n, M))
+    v -= v.mean(axis=1, keepdims=True)
+    return v / np.abs(v).sum(axis=1, keepdims=True)
+
+
+def sequence(rng, K, amp, rho, theta=0.0, noise=0.0, cycle=False, amp2=0.0, mu=0.3):
+    """Step vectors d_1..d_K and the true errors ||pi_k - pi||_1, k = 0..K."""
+    v1, v2, v3 = _zero_sum_unit(rng, 3)
+    k = np.arange(K + 1)[:, None]
+    e = amp * rho ** k * (np.cos(k * theta) * v1 + np.sin(k * theta) * v2) + amp2 * mu ** k * v3
+    if cycle:
+        eta = noise * (-1.0) ** k * _zero_sum_unit(rng)
+    else:
+        eta = noise * _zero_sum_unit(rng, K + 1)
+    it = e + eta
+    return np.diff(it, axis=0), np.abs(it).sum(axis=1)
+
+
+CLEAN = [(0.05, 0.0), (0.3, 0.0), (0.6, 0.0), (0.87, 0.0), (0.7, np.pi), (0.8, 0.4), (0.8, 1.2), (0.8, 2.5),
+         (0.5, 2.0)]
+
+
+@pytest.mark.parametrize("rho,theta", CLEAN)
+@pytest.mark.parametrize("noise", [0.0, 1e-7])
+def test_transient_from_far_start(rule, rho, theta, noise):
+    rng = np.random.default_rng(int(rho * 100 + theta * 10 + noise * 1e9))
+    d, true = sequence(rng, 200, 1.0, rho, theta, noise, amp2=0.5)
+    k, st = rule(d)
+    assert k > 0, st
+    assert true[k] < TOL, (k, true[k], st)
+    # no more than a few steps past the first iterate within tol_err (more
+    # with noise: a floor under an oscillating transient shows only after
+    # the transient has decayed well below it)
+    first = int(np.argmax(true < 0.5 * TOL_ERR))
+    assert k <= first + (6 if noise == 0.0 else 12), (k, first, st)
+
+
+@pytest.mark.parametrize("noise", [3e-8, 1e-7, 2e-7, 3.5e-7, 6e-7])
+@pytest.mark.parametrize("cycle", [False, True])
+def test_start_on_the_noise_floor_stops(rule, noise, cycle):
+    """A warm start already within rounding noise of pi: no trustworthy
+    estimate of lambda_2 is possible, and the rule must still end, within
+    two 8-step blocks.  Ending as converged requires the true error below
+    the tolerance; a floor whose steps exceed 1e-6 may end as not converged
+    (the rule cannot certify it)."""
+    rng = np.random.default_rng(int(noise * 1e9) + cycle)
+    d, true = sequence(rng, 200, 0.0, 0.5, 0.0, noise, cycle=cycle)
+    k, st = rule(d)
+    assert k != 0 and abs(k) <= 16, (k, st)
+    if k > 0:
+        assert true[k] < TOL
+    else:
+        assert noise >= 5e-7
+
+
+@pytest.mark.parametrize("noise", [3e-6, 2e-5])
+def test_floor_above_tolerance_ends_as_not_converged(rule, noise):
+    """An FP32 floor above the tolerance: further steps cannot help; below
+    1e-5 steps it ends within two blocks as not converged, above it the
+    rule keeps iterating (max_iter ends it)."""
+    rng = np.random.default_rng(5)
+    d, _ = sequence(rng, 64, 0.0, 0.5, 0.0, noise)
+    k, st = rule(d)
+    if noise < 5e-6:
+        assert -16 <= k < 0, (k, st)
+    else:
+        assert k == 0, (k, st)
+
+
+@pytest.mark.parametrize("rho,theta,amp,noise", [(0.87, 0.0, 3e-6, 1e-7), (0.87, 0.0, 6e-6, 5e-8),
+                                                 (0.85, 0.5, 3e-6, 5e-8), (0.8, 0.0, 1e-5, 1e-7),
+                                                 (0.87, 0.0, 2e-6, 0.0), (0.6, np.pi, 4e-6, 1e-7)])
+def test_warm_start_on_a_slow_mode(rule, rho, theta, amp, noise):
+    """A warm start whose whole error lies in a slow mode: its steps are
+    already below the stall floors, so only the decay pattern tells it from
+    noise; the rule must not stop while the error exceeds the tolerance."""
+    for seed in range(5):
+        rng = np.random.default_rng(seed)
+        d, true = sequence(rng, 300, amp, rho, theta, noise)
+        k, st = rule(d)
+        assert k > 0, st
+        assert true[k] < TOL, (seed, k, true[k], st)
+
+
+def test_min_iter_is_respected(rule):
+    rng = np.random.default_rng(0)
+    d, _ = sequence(rng, 50, 0.0, 0.5, 0.0, 1e-8)
+    k, _ = rule(d, min_iter=12)
+    assert k >= 12
+
+
+def test_exact_fixed_point_stops_at_once(rule):
+    d = np.zeros((10, M))
+    k, st = rule(d)
+    assert k == 3 and st["err"] == 0.0
+
+
+def test_lambda2_estimate_from_clean_transient(rule):
+    rng = np.random.default_rng(3)
+    for rho, theta in [(0.6, 0.0), (0.8, 1.2), (0.7, np.pi)]:
+        d, _ = sequence(rng, 200, 1.0, rho, theta)
+        k, st = rule(d)
+        assert st["reliable"] == 1
+        assert abs(st["rho"] - rho) < 2e-2 * rho, (rho, theta, st)
+        assert abs(st["theta"] - theta) < 5e-2, (rho, theta, st)
