@@ -83,6 +83,12 @@ def _load():
         lib.oracle_batch_stationary.restype = ctypes.c_int
         lib.oracle_mc_deadtime.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _i64p]
         lib.oracle_mc_deadtime.restype = ctypes.c_int64
+        _u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.oracle_philox4x64.argtypes = [_u64p, _u64p, _u64p]
+        lib.oracle_philox4x64.restype = None
+        lib.oracle_mc_philox.argtypes = [_dp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int32, ctypes.c_int64,
+                                         ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]
+        lib.oracle_mc_philox.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -239,3 +245,31 @@ def mc_histogram(p, n_periods: int, rng: np.random.Generator) -> np.ndarray:
     X = mc_registrations(p, n_periods, rng)
     k = np.minimum((X * N / float(p["t_r"])).astype(np.int64), N - 1)
     return np.bincount(k, minlength=N).astype(np.float64)
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """One Philox4x64-10 block (Salmon et al., SC 2011): four 64-bit words."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(4, dtype=np.uint64)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    _load().oracle_philox4x64(_ptr(c, u64p), _ptr(k, u64p), _ptr(out, u64p))
+    return out
+
+
+def mc_philox_histograms(pixels, runs: int, cycles: int, seed: int, nthreads: int | None = None):
+    """Counter-based event Monte Carlo (the Monte Carlo reference of Sec. 5,
+    exactly specified in spl_oracle.c): per-run registration histograms.
+    Returns (hist uint32 packed [runs * N_k per pixel], offsets [n+1] of the
+    bins, so run r of pixel k is hist[runs*off[k] + r*N_k : + N_k])."""
+    n = len(pixels)
+    thetas = np.ascontiguousarray(np.stack([_theta(p) for p in pixels]), dtype=np.float64)
+    Ns = np.ascontiguousarray([int(p["n_bins"]) for p in pixels], dtype=np.int32)
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(Ns)
+    hist = np.zeros(int(offsets[-1]) * runs, dtype=np.uint32)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    _load().oracle_mc_philox(_ptr(thetas), _ptr(Ns, _i32p), n, _ptr(offsets, _i64p), int(runs), int(cycles),
+                             ctypes.c_uint64(int(seed)), int(nthreads), _ptr(hist, ctypes.POINTER(ctypes.c_uint32)))
+    return hist, offsets

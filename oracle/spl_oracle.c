@@ -279,3 +279,178 @@ int64_t oracle_mc_deadtime(const double *T, int64_t n, double t_d, int64_t *idx_
     }
     return m;
 }
+
+/*
+ * Counter-based event Monte Carlo: the Monte Carlo reference of Sec. 5
+ * (Fig. 3b/3c) as an exactly specified random experiment, so that a GPU
+ * implementation drawing the same numbers can be compared bin by bin.
+ *
+ * Random words: Philox4x64-10 (Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC 2011): ten rounds of two 64x64->128
+ * multiplications on a 4-word counter with a 2-word key bumped by the Weyl
+ * constants between rounds.
+ *
+ * The experiment for pixel k (theta, N) and run r:
+ *   key = (seed, k * 2^32 + r); the uniforms of cycle c are the words of
+ *   Philox(counter = (c, b, 0, 0)), b = 0, 1, ..., consumed in order, each
+ *   mapped to u = ((w >> 11) + 1/2) 2^-53 in (0, 1).
+ *   Per cycle: n_s = Poisson(S) by inversion of one uniform (sequential CDF
+ *   search from exp(-S), term recurrence p <- (p * S) / k, at most 64); n_s
+ *   signal photons t = tau + sigma * sqrt(-2 ln u1) cos(2 pi u2), kept if
+ *   0 <= t < t_r (the pulse of Eq. 1 truncated to one period); then
+ *   n_b = Poisson(B) the same way and n_b background photons t = u t_r.
+ *   Arrivals are sorted (stable: signal before background on ties) and pass
+ *   the non-paralysable dead-time filter of Sec. 2.2: a photon at t registers
+ *   if t >= ready (time relative to this cycle's start), then ready = t + t_d;
+ *   ready carries over to the next cycle as ready - t_r, and starts at -inf.
+ *   A registration at t counts in bin floor(t N / t_r) (clamped to N - 1).
+ * All arithmetic is FP64 with no contraction.
+ */
+static const uint64_t PHILOX_M0 = 0xD2E7470EE14C6C93ULL, PHILOX_M1 = 0xCA5A826395121157ULL;
+static const uint64_t PHILOX_W0 = 0x9E3779B97F4A7C15ULL, PHILOX_W1 = 0xBB67AE8584CAA73BULL;
+
+void oracle_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out)
+{
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        const unsigned __int128 p0 = (unsigned __int128)PHILOX_M0 * c0;
+        const unsigned __int128 p1 = (unsigned __int128)PHILOX_M1 * c2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+typedef struct {
+    uint64_t key[2];
+    uint64_t cycle, block;
+    uint64_t buf[4];
+    int pos;
+} mc_stream_t;
+
+static double mc_uniform(mc_stream_t *s)
+{
+    if (s->pos == 4) {
+        const uint64_t ctr[4] = {s->cycle, s->block, 0, 0};
+        oracle_philox4x64(ctr, s->key, s->buf);
+        s->block += 1;
+        s->pos = 0;
+    }
+    const uint64_t w = s->buf[s->pos++];
+    return ((double)(w >> 11) + 0.5) * 0x1p-53;
+}
+
+enum { MC_CAP = 64 };
+
+static int mc_poisson(double mean, double u)
+{
+    double p = exp(-mean), F = p;
+    int k = 0;
+    while (u > F && k < MC_CAP) {
+        k += 1;
+        p = (p * mean) / (double)k;
+        F = F + p;
+    }
+    return k;
+}
+
+/* One run: cycles laser cycles of pixel k, histogram added into hist[N]. */
+static void mc_run(const double *th, int N, uint64_t seed, uint64_t k, uint64_t r, int64_t cycles,
+                   uint32_t *hist)
+{
+    const double t_r = th[TH_TR], t_d = th[TH_TD], tau = th[TH_TAU], sigma = th[TH_SIGMA];
+    const double S = th[TH_S], B = th[TH_B];
+    const double two_pi = 2.0 * M_PI;
+    mc_stream_t s;
+    s.key[0] = seed;
+    s.key[1] = (k << 32) | r;
+    double ready = -INFINITY;
+    double t[2 * MC_CAP];
+    for (int64_t c = 0; c < cycles; ++c) {
+        s.cycle = (uint64_t)c;
+        s.block = 0;
+        s.pos = 4;
+        int n = 0;
+        const int ns = mc_poisson(S, mc_uniform(&s));
+        for (int i = 0; i < ns; ++i) {
+            const double u1 = mc_uniform(&s), u2 = mc_uniform(&s);
+            const double z = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+            const double x = tau + sigma * z;
+            if (x >= 0.0 && x < t_r) t[n++] = x;
+        }
+        const int nb = mc_poisson(B, mc_uniform(&s));
+        for (int i = 0; i < nb; ++i) t[n++] = mc_uniform(&s) * t_r;
+        /* insertion sort, stable */
+        for (int i = 1; i < n; ++i) {
+            const double x = t[i];
+            int j = i - 1;
+            while (j >= 0 && t[j] > x) { t[j + 1] = t[j]; --j; }
+            t[j + 1] = x;
+        }
+        for (int i = 0; i < n; ++i) {
+            if (t[i] >= ready) {
+                int b = (int)((t[i] * (double)N) / t_r);
+                if (b > N - 1) b = N - 1;
+                hist[b] += 1;
+                ready = t[i] + t_d;
+            }
+        }
+        ready = ready - t_r;
+    }
+}
+
+typedef struct {
+    const double *thetas;
+    const int32_t *Ns;
+    const int64_t *offsets;
+    int32_t n, runs;
+    int64_t cycles;
+    uint64_t seed;
+    uint32_t *hist;
+    int64_t next;
+    pthread_mutex_t lock;
+} mc_job_t;
+
+static void *mc_worker(void *arg)
+{
+    mc_job_t *job = (mc_job_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        const int64_t item = job->next++;
+        pthread_mutex_unlock(&job->lock);
+        if (item >= (int64_t)job->n * job->runs) break;
+        const int32_t k = (int32_t)(item / job->runs), r = (int32_t)(item % job->runs);
+        const int N = job->Ns[k];
+        uint32_t *h = job->hist + (int64_t)job->runs * job->offsets[k] + (int64_t)r * N;
+        memset(h, 0, sizeof(uint32_t) * (size_t)N);
+        mc_run(job->thetas + 6 * (int64_t)k, N, job->seed, (uint64_t)k, (uint64_t)r, job->cycles, h);
+    }
+    return NULL;
+}
+
+/* Histograms of all (pixel, run) pairs: run r of pixel k at
+ * hist[runs * offsets[k] + r * N_k .. + N_k). */
+int oracle_mc_philox(const double *thetas, const int32_t *Ns, int32_t n, const int64_t *offsets, int32_t runs,
+                     int64_t cycles, uint64_t seed, int32_t nthreads, uint32_t *hist)
+{
+    mc_job_t job;
+    job.thetas = thetas; job.Ns = Ns; job.offsets = offsets; job.n = n; job.runs = runs;
+    job.cycles = cycles; job.seed = seed; job.hist = hist; job.next = 0;
+    pthread_mutex_init(&job.lock, NULL);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *tids = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int started = 0;
+    for (int i = 0; i < nthreads; ++i)
+        if (pthread_create(&tids[i], NULL, mc_worker, &job) == 0) ++started;
+    if (started == 0) mc_worker(&job);
+    for (int i = 0; i < started; ++i) pthread_join(tids[i], NULL);
+    free(tids);
+    pthread_mutex_destroy(&job.lock);
+    return started;
+}

@@ -308,6 +308,7 @@ struct BatchFlux {
     double bgK_lo, bgK_hi;   // bg * exp(Lambda/2 - S G) on either side of the pulse
     double K_half;           // exp(Lambda/2)
     float bg_f;
+    float uK_lo, uK_hi;      // tail row factors exp(S G - Lambda/2) for B = 0 (where g = 1 and w = 0)
     int j_lo, j_hi;          // bins with |z| <= 9 (the pulse); the rest are tail bins
 };
 
@@ -325,6 +326,8 @@ __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f
     f.bgK_lo = f.bg * exp(0.5 * fc.Lambda + p.S * fc.Phi0);             // G = -Phi0 (left of the pulse)
     f.bgK_hi = f.bg * exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));     // G = 1 - Phi0 (right of the pulse)
     f.K_half = exp(0.5 * fc.Lambda);
+    f.uK_lo = (float)exp(-0.5 * fc.Lambda - p.S * fc.Phi0);
+    f.uK_hi = (float)exp(p.S * (1.0 - fc.Phi0) - 0.5 * fc.Lambda);
     // pulse bins: s_j within 9 sigma of tau, i.e. j in [(tau - 9 sigma)/Delta - 1/2, (tau + 9 sigma)/Delta - 1/2]
     const double lo = (p.tau - kTailZ * p.sigma) / fc.delta - 0.5;
     const double hi = (p.tau + kTailZ * p.sigma) / fc.delta - 0.5;
@@ -342,6 +345,12 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
     if (j < f.j_lo || j > f.j_hi) {
         w = (float)((j < f.j_lo ? f.bgK_lo : f.bgK_hi) * g);
         lam_f = f.bg_f;
+        if (!(f.bg > 0.0)) {
+            // no background: lambda_j = w_j = 0 here, and u_j = exp(F_j - Lambda/2)
+            // is the side's constant (g = 1 when B = 0)
+            u = j < f.j_lo ? f.uK_lo : f.uK_hi;
+            return;
+        }
     } else {
         const double s = ((double)j + 0.5) * f.delta;
         const double z = (s - p.tau) * f.inv_sigma;

@@ -270,6 +270,25 @@ def test_restart_from_converged_result_ends(spl, pass_kind):
         assert _l1(o[off[k]:off[k + 1]], refs[roff[r]:roff[r + 1]]) < L1_TOL
 
 
+@pytest.mark.parametrize("pass_kind", ["dense", "structured"])
+def test_zero_background(spl, pass_kind):
+    """B = 0 (S > 0, allowed by the S + B > 0 rule): lambda vanishes outside
+    the pulse, those columns of P~ are zero and pi is zero there (transient
+    bins, one recurrent class).  The row factor u_j = exp(F_j - Lambda/2) stays
+    finite in the tails and pi matches the oracle."""
+    pk = spl.SPL_PASS_DENSE if pass_kind == "dense" else spl.SPL_PASS_STRUCTURED
+    px = np.concatenate([W.pixel(n, t_d, 30.0, sg, S, 0.0) for n, t_d, sg, S in
+                         [(256, 75.0, 0.5, 0.5), (256, 95.0, 1.0, 10.0), (1000, 75.0, 0.3, 5.0),
+                          (777, 130.0, 0.8, 2.0), (2000, 20.0, 0.2, 8.0)]])
+    out, off, reps = spl.batch_stationary(px, pass_kind=pk)
+    assert np.all(reps["status"] == 0), reps["status"]
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(o))
+    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px), tol=1e-12)
+    for k in range(len(px)):
+        assert _l1(o[off[k]:off[k + 1]], refs[roff[k]:roff[k + 1]]) < L1_TOL
+
+
 def test_batch_host_entry_point(spl):
     px = W.array_pixels(50, seed=15, n_bins=700)
     d, off, _ = spl.batch_stationary(px)
