@@ -444,6 +444,50 @@ def run_gpu(args):
             "lambda2_abs_range": [float(lam2[:, 0].min()), float(lam2[:, 0].max())],
             "note": "orthogonal iteration on the deflated O(N) operator, 60 steps, N = 256 (the paper's grid resolution)"}
 
+    # accuracy across (S, B) against the event Monte Carlo (Sec. 5, Fig. 3c):
+    # 21 x 21 grid over [0, 10]^2 at 256 bins, 25 runs x 50,000 cycles each
+    if not args.no_mc and rank == 0:
+        g = W.accuracy_grid()
+        runs, cycles, nb = 25, 50000, 256
+        spl.mc_histograms(g[:4], 2, 1000, seed=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h, _ = spl.mc_histograms(g, runs, cycles, seed=3)
+        mc_s = time.perf_counter() - t0
+        H = h.cpu().numpy().view(np.uint32).reshape(len(g), runs, nb).sum(axis=1).astype(np.float64)
+        nreg = H.sum(axis=1)
+
+        def agreement(flux_kind):
+            pig, _, rg = spl.batch_stationary(g, tol=TOL, flux_kind=flux_kind)
+            Pg = pig.cpu().numpy().astype(np.float64).reshape(len(g), nb)
+            l1 = np.abs(Pg - H / nreg[:, None]).sum(axis=1)
+            # L1 distance a multinomial sample of the same size would show from Pg
+            noise = np.sqrt(2.0 / np.pi) * np.sqrt(Pg * (1.0 - Pg) / nreg[:, None]).sum(axis=1)
+            chi = []
+            for k in range(len(g)):
+                E = nreg[k] * Pg[k]
+                m = E >= 5
+                chi.append(float((((H[k][m] - E[m]) ** 2) / E[m]).sum() / max(1, m.sum() - 1)))
+            chi = np.array(chi)
+            worst = int(np.argmax(l1 / noise))
+            return {"l1_median": float(np.median(l1)), "l1_max": float(l1.max()),
+                    "mc_noise_l1_median": float(np.median(noise)),
+                    "l1_over_noise_median": float(np.median(l1 / noise)),
+                    "l1_over_noise_max": float((l1 / noise).max()),
+                    "chi2_per_dof_median": float(np.median(chi)), "chi2_per_dof_max": float(chi.max()),
+                    "points_within_2x_noise": int(np.sum(l1 < 2 * noise)),
+                    "worst_point": {"S": float(g["S"][worst]), "B": float(g["B"][worst])}}
+
+        extra["mc_accuracy_grid"] = {
+            "points": int(len(g)), "n_bins": nb, "runs": runs, "cycles_per_run": cycles,
+            "mc_seconds": mc_s, "mc_cycles_per_second": len(g) * runs * cycles / mc_s,
+            "registrations": float(nreg.sum()),
+            "point_flux": agreement(spl.SPL_FLUX_POINT),
+            "bin_integrated": agreement(spl.SPL_FLUX_BININT),
+            "workload": "S, B on a 21 x 21 grid over [0, 10] without (0, 0), t_d = 75, tau = 30, sigma = 0.5, "
+                        "t_r = 100; pmfs from the batch solver (dense step), the paper's point flux and the "
+                        "bin-integrated variant"}
+
     # materialised vs matrix-free power step on one N = 10000 pixel (400 MB P)
     if not args.no_highres and rank == 0:
         hp = W.pixel(10000, 75.0, 30.0, 0.3, 0.5, 0.5)
@@ -542,6 +586,7 @@ def main():
     ap.add_argument("--no-structured", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-spectral", action="store_true")
+    ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--audit", type=int, default=64, help="pixels of the timed output checked against the oracle")
     ap.add_argument("--train-pixels", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=20)

@@ -148,6 +148,14 @@ typedef enum {
                                  (O(N) per step; row sums by prefix and suffix scans) */
 } spl_pass_kind_t;
 
+/* Column weights of P~ (how the detection density enters bin j). */
+typedef enum {
+    SPL_FLUX_POINT = 0,       /* the paper's form (Sec. 3.4): lambda(s_j) exp(-F(s_j)) at the bin centre */
+    SPL_FLUX_BININT = 1,      /* an ablation beyond the paper: the exact integral of the detection density
+                                 over the bin, exp(-F(j Delta)) - exp(-F((j+1) Delta)) (the point form is its
+                                 midpoint rule; the two agree to O(Delta^2)) */
+} spl_flux_kind_t;
+
 /* Options for spl_batch_stationary_ex. */
 typedef struct {
     int32_t warm_kind;        /* spl_warm_kind_t, used when d_warm != NULL */
@@ -156,6 +164,7 @@ typedef struct {
     int32_t threads;          /* threads per block, 0 = library default */
     int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
     int32_t pass_kind;        /* spl_pass_kind_t */
+    int32_t flux_kind;        /* spl_flux_kind_t */
 } spl_batch_opts_t;
 
 /* spl_batch_stationary with options (opts may be NULL for the defaults). */
@@ -177,6 +186,28 @@ SPL_API spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int32_
  */
 SPL_API spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t n, int32_t subspace_iters,
                                         float *d_out, void *stream);
+
+/*
+ * Event Monte Carlo reference histograms (Sec. 5, Fig. 3b/3c; the detector
+ * model of Sec. 2.2): for each pixel, `runs` independent runs of `cycles`
+ * laser cycles each.  Per cycle, Poisson(S) Gaussian signal photons (kept
+ * inside [0, t_r)) and Poisson(B) uniform background photons, in time order,
+ * pass a non-paralysable dead time t_d that carries across cycles; each
+ * registration counts in bin floor(t N / t_r).  Random numbers: Philox4x64-10
+ * with key (seed, k 2^32 + r) for run r of pixel k and counter
+ * (cycle, block, 0, 0); the experiment is exactly specified (FP64, no
+ * contraction), so the same seed gives the same histograms on any
+ * implementation of it.  shift_override is ignored.
+ *   d_hist : device uint32, run r of pixel k at runs * off_k + r * N_k,
+ *            off_k = sum of n_bins of pixels 0..k-1 (caller-owned, fully
+ *            written).
+ * Limits: n_bins <= 16384, S <= 16, B <= 16 (at most 64 photons per source
+ * and cycle; more has probability < 1e-18), n * runs < 2^31.
+ * Errors: SPL_EINVAL for invalid pixels or limits, SPL_ENOMEM, SPL_ECUDA.
+ * Allocates a small parameter buffer; synchronises `stream`.
+ */
+SPL_API spl_status_t spl_mc_histograms(const spl_pixel_t *h_pixels, int32_t n, int32_t runs, int64_t cycles,
+                                       uint64_t seed, uint32_t *d_hist, void *stream);
 
 /* Device time in ms of the batch kernel of the last spl_batch_stationary_ex
  * call on the current device that set time_kernel (events recorded on that

@@ -67,6 +67,8 @@ def _load():
         lib.oracle_shift_l.restype = ctypes.c_int64
         lib.oracle_build_seq.argtypes = [_dp, ctypes.c_int32, _dp]
         lib.oracle_build_seq.restype = None
+        lib.oracle_build_binint.argtypes = [_dp, ctypes.c_int32, ctypes.c_int64, _dp]
+        lib.oracle_build_binint.restype = None
         lib.oracle_build_reparam.argtypes = [_dp, ctypes.c_int32, ctypes.c_int64, _dp]
         lib.oracle_build_reparam.restype = None
         lib.oracle_normalize_rows.argtypes = [ctypes.c_int32, _dp]
@@ -89,6 +91,9 @@ def _load():
         lib.oracle_mc_philox.argtypes = [_dp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int32, ctypes.c_int64,
                                          ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]
         lib.oracle_mc_philox.restype = ctypes.c_int
+        lib.oracle_mc_philox_run.argtypes = [_dp, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32)]
+        lib.oracle_mc_philox_run.restype = None
         _lib = lib
         return lib
 
@@ -161,6 +166,16 @@ def build_reparam(p, shift: int) -> np.ndarray:
     return P
 
 
+def build_binint(p, shift: int) -> np.ndarray:
+    """Unnormalised P of the bin-integrated variant (exact integral of the
+    detection density over each bin instead of its midpoint value)."""
+    N = int(p["n_bins"])
+    th = _theta(p)
+    P = np.empty((N, N), dtype=np.float64)
+    _load().oracle_build_binint(_ptr(th), N, int(shift), _ptr(P))
+    return P
+
+
 def normalize_rows(P: np.ndarray) -> np.ndarray:
     """Row-normalised copy P~ (Sec. 2.3)."""
     Q = np.ascontiguousarray(P, dtype=np.float64).copy()
@@ -184,13 +199,19 @@ def power(Pt: np.ndarray, tol: float = 1e-12, max_iter: int = 100000, start=None
     return out, it, last.value
 
 
-def stationary(p, tol: float = 1e-12, max_iter: int = 100000, shift=None) -> np.ndarray:
+def stationary(p, tol: float = 1e-12, max_iter: int = 100000, shift=None, flux: str = "point") -> np.ndarray:
     """Stationary pmf of one pixel.  shift=None: sequential construction
-    (shift-then-quantise).  shift=k: reparameterised build with row shift k."""
+    (shift-then-quantise).  shift=k: reparameterised build with row shift k.
+    flux="binint" (needs a shift): the bin-integrated variant."""
     N = int(p["n_bins"])
     th = _theta(p)
     out = np.empty(N, dtype=np.float64)
-    mode, sh = (0, 0) if shift is None else (1, int(shift))
+    if flux == "binint":
+        if shift is None:
+            raise ValueError("the bin-integrated variant takes an explicit shift")
+        mode, sh = 2, int(shift)
+    else:
+        mode, sh = (0, 0) if shift is None else (1, int(shift))
     it = _load().oracle_stationary(_ptr(th), N, mode, sh, float(tol), int(max_iter), _ptr(out))
     if it < 0:
         raise RuntimeError(f"oracle power iteration failed (status {it})")
@@ -273,3 +294,14 @@ def mc_philox_histograms(pixels, runs: int, cycles: int, seed: int, nthreads: in
     _load().oracle_mc_philox(_ptr(thetas), _ptr(Ns, _i32p), n, _ptr(offsets, _i64p), int(runs), int(cycles),
                              ctypes.c_uint64(int(seed)), int(nthreads), _ptr(hist, ctypes.POINTER(ctypes.c_uint32)))
     return hist, offsets
+
+
+def mc_philox_run(p, k: int, r: int, cycles: int, seed: int) -> np.ndarray:
+    """Histogram of run r of the pixel at position k of a launch (the key
+    depends on both), from the same experiment as mc_philox_histograms."""
+    th = _theta(p)
+    N = int(p["n_bins"])
+    h = np.zeros(N, dtype=np.uint32)
+    _load().oracle_mc_philox_run(_ptr(th), N, ctypes.c_uint64(int(seed)), ctypes.c_uint64(int(k)),
+                                 ctypes.c_uint64(int(r)), int(cycles), _ptr(h, ctypes.POINTER(ctypes.c_uint32)))
+    return h

@@ -150,6 +150,36 @@ void oracle_build_reparam(const double *th, int32_t N, int64_t shift, double *P)
     }
 }
 
+/*
+ * Bin-integrated variant of Eq. 6 (an ablation beyond the paper, which takes
+ * the point flux lambda(s_j) at the bin centre, Sec. 3.4).  Entry (i, j) is
+ * the probability, for a detector re-armed at the centre s_p of bin
+ * p = (i + shift) mod N, that its next registration falls anywhere in bin
+ * j = [j Delta, (j+1) Delta): the exact integral of lambda(t) exp(-(F(t) - F(s_p)))
+ * over the bin, i.e. exp(F(s_p) - F(j Delta)) - exp(F(s_p) - F((j+1) Delta)),
+ * times exp(-Lambda) when the bin is only reached after the period wraps
+ * (p > j).  The point form is this integral by the midpoint rule.  Same
+ * unnormalised scale as oracle_build_reparam (divided by 1 - exp(-Lambda)
+ * and by Delta).
+ */
+void oracle_build_binint(const double *th, int32_t N, int64_t shift, double *P)
+{
+    const double Delta = th[TH_TR] / (double)N;
+    const double Lambda = oracle_Lambda(th);
+    const double norm = -expm1(-Lambda) * Delta;
+    int64_t sh = shift % N; if (sh < 0) sh += N;
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t p = (i + sh) % N;
+        const double F_p = oracle_F(th, ((double)p + 0.5) * Delta);
+        for (int64_t j = 0; j < N; ++j) {
+            const double F_lo = oracle_F(th, (double)j * Delta);
+            const double F_hi = oracle_F(th, (double)(j + 1) * Delta);
+            const double wrap = (p > j) ? exp(-Lambda) : 1.0;
+            P[i * N + j] = wrap * exp(F_p - F_lo) * -expm1(F_lo - F_hi) / norm;
+        }
+    }
+}
+
 /* Row normalisation P -> P~ (Sec. 2.3).  Returns 0, or -1 on a zero row. */
 int oracle_normalize_rows(int32_t N, double *P)
 {
@@ -213,6 +243,7 @@ int oracle_stationary(const double *th, int32_t N, int32_t shift_mode, int64_t s
     double *P = (double *)malloc(sizeof(double) * (size_t)N * (size_t)N);
     if (!P) return -2;
     if (shift_mode == 0) oracle_build_seq(th, N, P);
+    else if (shift_mode == 2) oracle_build_binint(th, N, shift, P);
     else oracle_build_reparam(th, N, shift, P);
     if (oracle_normalize_rows(N, P) != 0) { free(P); return -3; }
     int it = oracle_power(N, P, tol, max_iter, NULL, pi_out, NULL);
@@ -453,4 +484,13 @@ int oracle_mc_philox(const double *thetas, const int32_t *Ns, int32_t n, const i
     free(tids);
     pthread_mutex_destroy(&job.lock);
     return started;
+}
+
+/* One (pixel k, run r) stream of the experiment above, histogram zeroed and
+ * filled: for checking sampled runs of a large launch. */
+void oracle_mc_philox_run(const double *theta, int32_t N, uint64_t seed, uint64_t k, uint64_t r, int64_t cycles,
+                          uint32_t *hist)
+{
+    memset(hist, 0, sizeof(uint32_t) * (size_t)N);
+    mc_run(theta, N, seed, k, r, cycles, hist);
 }

@@ -21,10 +21,18 @@ namespace {
 
 thread_local char g_cuda_err[256] = "";
 
-spl_status_t cuda_fail(cudaError_t e, const char *where) {
+}  // namespace
+
+// The last CUDA failure of this thread, for spl_last_cuda_error (every
+// translation unit of the library records through here).
+spl_status_t spl::note_cuda_error(cudaError_t e, const char *where) {
     snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
     return SPL_ECUDA;
 }
+
+namespace {
+
+spl_status_t cuda_fail(cudaError_t e, const char *where) { return note_cuda_error(e, where); }
 
 #define SPL_CU(expr)                                                   \
     do {                                                               \
@@ -558,7 +566,7 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
-                       cudaStream_t s, bool time_kernel = false, int structured = 0) {
+                       cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0) {
     const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
     if (threads != 256 && threads != 512) return SPL_EINVAL;
     const int npad = batch_pad_len(nmax);
@@ -597,6 +605,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);
     a.structured = structured;
+    a.flux_kind = flux_kind;
     if (time_kernel) {
         if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
@@ -657,8 +666,10 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     const bool timed = opts && opts->time_kernel;
     const int structured = opts ? opts->pass_kind : 0;
     if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    const int flux_kind = opts ? opts->flux_kind : 0;
+    if (flux_kind != SPL_FLUX_POINT && flux_kind != SPL_FLUX_BININT) return SPL_EINVAL;
     st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed,
-                   structured);
+                   structured, flux_kind);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the

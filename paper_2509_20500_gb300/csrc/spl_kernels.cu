@@ -310,7 +310,19 @@ struct BatchFlux {
     float bg_f;
     float uK_lo, uK_hi;      // tail row factors exp(S G - Lambda/2) for B = 0 (where g = 1 and w = 0)
     int j_lo, j_hi;          // bins with |z| <= 9 (the pulse); the rest are tail bins
+    double half_z;           // Delta / (2 sigma)
+    double tail_ratio;       // bin-integrated / point column factor outside the pulse, 2 sinh(beta/2) / beta
 };
+
+// Phi(b) - Phi(a) for a <= b, from the side of the distribution where both
+// tails are small, so a narrow interval far out keeps its relative accuracy.
+__device__ __forceinline__ double cdf_diff(double a, double b) {
+    constexpr double k = 0.70710678118654752440;
+    if (a >= 0.0) return 0.5 * (erfc(a * k) - erfc(b * k));
+    if (b <= 0.0) return 0.5 * (erfc(-b * k) - erfc(-a * k));
+    return 1.0 - 0.5 * (erfc(b * k) + erfc(-a * k));
+}
+
 
 __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f, double *t_lo, double *t_hi,
                                                  int nblk) {
@@ -328,6 +340,8 @@ __device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f
     f.K_half = exp(0.5 * fc.Lambda);
     f.uK_lo = (float)exp(-0.5 * fc.Lambda - p.S * fc.Phi0);
     f.uK_hi = (float)exp(p.S * (1.0 - fc.Phi0) - 0.5 * fc.Lambda);
+    f.half_z = 0.5 * fc.delta / p.sigma;
+    f.tail_ratio = f.beta > 0.0 ? 2.0 * sinh(0.5 * f.beta) / f.beta : 1.0;
     // pulse bins: s_j within 9 sigma of tau, i.e. j in [(tau - 9 sigma)/Delta - 1/2, (tau + 9 sigma)/Delta - 1/2]
     const double lo = (p.tau - kTailZ * p.sigma) / fc.delta - 0.5;
     const double hi = (p.tau + kTailZ * p.sigma) / fc.delta - 0.5;
@@ -343,7 +357,8 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
                                                const double *t_hi, int j, float &w, float &u, float &lam_f) {
     const double g = t_hi[j >> 6] * t_lo[j & 63];                // exp(-B (j + 1/2) / N)
     if (j < f.j_lo || j > f.j_hi) {
-        w = (float)((j < f.j_lo ? f.bgK_lo : f.bgK_hi) * g);
+        const double wd = (j < f.j_lo ? f.bgK_lo : f.bgK_hi) * g;
+        w = (float)wd;
         lam_f = f.bg_f;
         if (!(f.bg > 0.0)) {
             // no background: lambda_j = w_j = 0 here, and u_j = exp(F_j - Lambda/2)
@@ -351,17 +366,45 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
             u = j < f.j_lo ? f.uK_lo : f.uK_hi;
             return;
         }
+        // Row factor u_j = exp(F_j - Lambda/2) = lambda_j / w_j.  It cancels
+        // exactly in the row-normalised matrix, so FP32 accuracy is enough.
+        u = lam_f / w;
     } else {
         const double s = ((double)j + 0.5) * f.delta;
         const double z = (s - p.tau) * f.inv_sigma;
         const double G = std_cdf(z) - f.Phi0;
         const double lam = p.S * exp(-0.5 * z * z) * f.gnorm + f.bg;
-        w = (float)(lam * exp(0.5 * f.Lambda - p.S * G) * g);
+        const double wd = lam * exp(0.5 * f.Lambda - p.S * G) * g;
+        w = (float)wd;
         lam_f = (float)lam;
+        u = lam_f / w;
     }
-    // Row factor u_j = exp(F_j - Lambda/2) = lambda_j / w_j.  It cancels
-    // exactly in the row-normalised matrix, so FP32 accuracy is enough.
-    u = lam_f / w;
+}
+
+// SPL_FLUX_BININT: replaces the point column factors w_j (in w and its copy
+// v) by the exact integral of the detection density over bin j instead of
+// its midpoint value.  With e_j = exp(Lambda/2 - F_j) = 1 / u_j:
+//   pulse bins  w_j = e_j exp(F_j - F_lo) (1 - exp(-m_j)) / Delta,
+//               F_j - F_lo the mass of the lower half bin, m_j the bin's mass;
+//   tail bins   w_j = w_j(point) 2 sinh(beta/2) / beta  (background only).
+// Each thread rewrites the bins it wrote in the flux loop.
+template <int NT>
+__device__ __forceinline__ void binint_pass(const PixelDev &p, const BatchFlux &f, const float *u, float *w,
+                                            float *v, int N) {
+    for (int j = threadIdx.x; j < N; j += NT) {
+        float x;
+        if (j < f.j_lo || j > f.j_hi) {
+            x = (float)((double)w[j] * f.tail_ratio);
+        } else {
+            const double z = (((double)j + 0.5) * f.delta - p.tau) * f.inv_sigma;
+            const double zl = z - f.half_z;
+            const double h_lo = p.S * cdf_diff(zl, z) + 0.5 * f.beta;
+            const double m = p.S * cdf_diff(zl, z + f.half_z) + f.beta;
+            x = (float)(exp(h_lo) * -expm1(-m) / (f.delta * (double)u[j]));
+        }
+        w[j] = x;
+        v[j] = x;
+    }
 }
 
 // Blocks per SM of the structured instantiation (no dense loops, few registers).
@@ -432,6 +475,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
             gu[j] = u;
             if (learned && j < N) spi[j] = logf(lam);   // flux prior of the learned start
         }
+        if (a.flux_kind) binint_pass<NT>(p, bf, gu, gw, sv, N);
         __syncthreads();
 
         // ---- row sums r'_k, rho_k = u_k / r'_k

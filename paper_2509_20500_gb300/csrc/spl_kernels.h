@@ -5,9 +5,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "spl.h"
 #include "spl_device.cuh"
 
 namespace spl {
+
+// Records a CUDA failure for spl_last_cuda_error; returns SPL_ECUDA.
+spl_status_t note_cuda_error(cudaError_t e, const char *where);
 
 // Device-resident state of one chain's iteration (single-pixel API).
 struct ChainState {
@@ -37,6 +41,7 @@ struct BatchArgs {
     int max_iter;
     int min_iter;
     int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
+    int flux_kind;           // spl_flux_kind_t: 0 point flux (Sec. 3.4), 1 bin-integrated
 };
 
 struct GemvArgs {

@@ -355,12 +355,7 @@ using namespace spl::mlp;
 
 namespace {
 
-thread_local char g_mlp_err[256] = "";
-
-spl_status_t mfail(cudaError_t e, const char *where) {
-    snprintf(g_mlp_err, sizeof(g_mlp_err), "%s: %s", where, cudaGetErrorString(e));
-    return SPL_ECUDA;
-}
+spl_status_t mfail(cudaError_t e, const char *where) { return note_cuda_error(e, where); }
 
 #define MCU(expr)                                          \
     do {                                                   \

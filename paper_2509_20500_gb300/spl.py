@@ -37,11 +37,13 @@ class spl_report_t(ctypes.Structure):
 
 class spl_batch_opts_t(ctypes.Structure):
     _fields_ = [("warm_kind", ctypes.c_int32), ("warm_ld", ctypes.c_int32), ("min_iter", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32), ("pass_kind", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32), ("pass_kind", ctypes.c_int32),
+                ("flux_kind", ctypes.c_int32)]
 
 
 SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
 SPL_PASS_DENSE, SPL_PASS_STRUCTURED = 0, 1
+SPL_FLUX_POINT, SPL_FLUX_BININT = 0, 1
 
 
 REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_l1", np.float32),
@@ -54,7 +56,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
-            "spl_chain_time_build", "spl_batch_spectral"]
+            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms"]
 
 _lib = None
 _lock = threading.Lock()
@@ -135,6 +137,9 @@ def lib():
         L.spl_batch_stationary_learned.restype = ctypes.c_int
         L.spl_batch_spectral.argtypes = [ctypes.POINTER(spl_pixel_t), i32, i32, vp, vp]
         L.spl_batch_spectral.restype = ctypes.c_int
+        L.spl_mc_histograms.argtypes = [ctypes.POINTER(spl_pixel_t), i32, i32, ctypes.c_int64, ctypes.c_uint64, vp,
+                                        vp]
+        L.spl_mc_histograms.restype = ctypes.c_int
         L.spl_chain_time_build.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.spl_chain_time_build.restype = ctypes.c_int
         L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
@@ -250,7 +255,7 @@ class Chain:
 def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
                      warm_kind: int = SPL_WARM_WEIGHTS, warm_ld: int = 0, min_iter: int = 1, threads: int = 0,
                      reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None,
-                     pass_kind: int = SPL_PASS_DENSE):
+                     pass_kind: int = SPL_PASS_DENSE, flux_kind: int = SPL_FLUX_POINT):
     """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
     import torch
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
@@ -263,7 +268,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
     arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
     opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)),
-                            int(pass_kind))
+                            int(pass_kind), int(flux_kind))
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
@@ -290,6 +295,21 @@ def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 
                                             _dptr(offsets), reps, _stream_ptr(stream))
     _check(st, "spl_batch_stationary_noalloc", (SPL_OK, SPL_ENOCONV))
     return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def mc_histograms(px: np.ndarray, runs: int, cycles: int, seed: int, out=None, stream=None):
+    """spl_mc_histograms: per-run registration histograms of the event Monte
+    Carlo, packed as run r of pixel k at runs*off[k] + r*N_k (int32 CUDA
+    tensor holding the uint32 counts).  Returns (hist, off)."""
+    import torch
+    px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+    off = offsets_of(px)
+    total = int(off[-1]) * int(runs)
+    if out is None:
+        out = torch.empty(max(1, total), dtype=torch.int32, device="cuda")
+    _check(lib().spl_mc_histograms(pixels_to_c(px), len(px), int(runs), int(cycles), ctypes.c_uint64(int(seed)),
+                                   _dptr(out), _stream_ptr(stream)), "spl_mc_histograms")
+    return out[:total], off
 
 
 def batch_spectral(px: np.ndarray, subspace_iters: int = 60, stream=None):
@@ -383,7 +403,8 @@ class MLP:
         return float(loss.value) if want_loss else None
 
     def batch_stationary(self, px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, out=None, offsets=None,
-                         reports: bool = True, c_pixels=None, pass_kind: int = SPL_PASS_DENSE):
+                         reports: bool = True, c_pixels=None, pass_kind: int = SPL_PASS_DENSE,
+                         flux_kind: int = SPL_FLUX_POINT):
         import torch
         n = len(px)
         off = offsets_of(px)
@@ -393,7 +414,7 @@ class MLP:
             out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
-        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind))
+        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind), int(flux_kind))
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
                                                 _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))

@@ -103,6 +103,20 @@ def uneven(n: int = 4096, seed: int = 4) -> np.ndarray:
     return a
 
 
+def accuracy_grid(n_bins: int = 256, steps: int = 21, t_d: float = 75.0, tau: float = 30.0,
+                  sigma: float = 0.5) -> np.ndarray:
+    """S, B on an even steps x steps grid over [0, 10] (the (0, 0) point
+    dropped: no photons), the other parameters fixed; row-major in S."""
+    g = np.linspace(0.0, 10.0, steps)
+    SB = [(S, B) for S in g for B in g if S + B > 0.0]
+    a = _empty(len(SB))
+    a["t_r"], a["t_d"], a["tau"], a["sigma"] = T_R, t_d, tau, sigma
+    a["S"] = [x[0] for x in SB]
+    a["B"] = [x[1] for x in SB]
+    a["n_bins"], a["shift_override"] = n_bins, -1
+    return a
+
+
 def random_small(n: int, seed: int, n_min: int = 2, n_max: int = 64) -> np.ndarray:
     """Small pixels with broad parameters (incl. t_d > t_r and t_d = 0) for
     exhaustive construction checks."""

@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(S):
 def test_struct_layouts(S):
     assert ctypes.sizeof(S.spl_pixel_t) == 56 == W.PIXEL_DTYPE.itemsize
     assert ctypes.sizeof(S.spl_report_t) == 24 == S.REPORT_DTYPE.itemsize
-    assert ctypes.sizeof(S.spl_batch_opts_t) == 24
+    assert ctypes.sizeof(S.spl_batch_opts_t) == 28
 
 
 def test_strerror_and_version(S):
@@ -74,6 +74,28 @@ def test_null_arguments_rejected(S):
     assert L.spl_batch_stationary(S.pixels_to_c(W.single()), 1, -1.0, 10, None, None, None, None, None) \
         == S.SPL_EINVAL
     L.spl_free(None)
+
+
+@pytest.mark.parametrize("bad", BAD[:-2] + [dict(S=16.5), dict(B=17.0), dict(n_bins=16385)])
+def test_mc_rejects_invalid_input_without_gpu(S, bad):
+    """spl_mc_histograms validates every pixel and its limits (at most 64
+    photons per source and cycle, 16384 bins) before touching the GPU."""
+    kw = dict(n_bins=100, t_d=75.0, tau=30.0, sigma=0.5, S=0.5, B=0.5)
+    kw.update(bad)
+    L = S.lib()
+    fake = ctypes.c_void_p(256)   # never dereferenced: validation fails first
+    assert L.spl_mc_histograms(S.pixels_to_c(W.pixel(**kw)), 1, 4, 100, 1, fake, None) == S.SPL_EINVAL
+
+
+def test_mc_rejects_bad_counts_without_gpu(S):
+    L = S.lib()
+    px = S.pixels_to_c(W.single())
+    fake = ctypes.c_void_p(256)
+    assert L.spl_mc_histograms(px, 1, 0, 100, 1, fake, None) == S.SPL_EINVAL
+    assert L.spl_mc_histograms(px, 1, 4, 0, 1, fake, None) == S.SPL_EINVAL
+    assert L.spl_mc_histograms(px, 0, 4, 100, 1, fake, None) == S.SPL_EINVAL
+    assert L.spl_mc_histograms(px, 1, 4, 100, 1, None, None) == S.SPL_EINVAL
+    assert L.spl_mc_histograms(None, 1, 4, 100, 1, fake, None) == S.SPL_EINVAL
 
 
 def test_oracle_and_library_share_nothing():

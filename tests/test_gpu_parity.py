@@ -280,13 +280,49 @@ def test_zero_background(spl, pass_kind):
     px = np.concatenate([W.pixel(n, t_d, 30.0, sg, S, 0.0) for n, t_d, sg, S in
                          [(256, 75.0, 0.5, 0.5), (256, 95.0, 1.0, 10.0), (1000, 75.0, 0.3, 5.0),
                           (777, 130.0, 0.8, 2.0), (2000, 20.0, 0.2, 8.0)]])
+    pixels = W.as_dicts(px)
+    # the paper's shift l against the reparameterised oracle (Eq. 6 with l) ...
     out, off, reps = spl.batch_stationary(px, pass_kind=pk)
     assert np.all(reps["status"] == 0), reps["status"]
     o = out.cpu().numpy().astype(np.float64)
     assert np.all(np.isfinite(o))
-    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px), tol=1e-12)
+    for k, p in enumerate(pixels):
+        ref = oracle.stationary(p, tol=1e-12, shift=oracle.shift_l(p))
+        assert _l1(o[off[k]:off[k + 1]], ref) < L1_TOL
+    # ... and the exact shift m against the sequential construction (Eq. 3-4);
+    # two of the pixels have non-integer q, where l = m + 1
+    pm = px.copy()
+    pm["shift_override"] = [oracle.shift_exact(p) for p in pixels]
+    out, off, reps = spl.batch_stationary(pm, pass_kind=pk)
+    o = out.cpu().numpy().astype(np.float64)
+    refs, roff, _, _ = oracle.batch_stationary(pixels, tol=1e-12)
     for k in range(len(px)):
         assert _l1(o[off[k]:off[k + 1]], refs[roff[k]:roff[k + 1]]) < L1_TOL
+
+
+@pytest.mark.parametrize("pass_kind", ["dense", "structured"])
+def test_bin_integrated_variant_vs_oracle(spl, pass_kind):
+    """SPL_FLUX_BININT (the bin integral of the detection density instead of
+    its midpoint value) against the oracle's direct build of that matrix:
+    array pixels at N = 2000, bright narrow pulses at the 2^8 bins of Fig. 3c
+    (half a bin is up to one sigma), B = 0, pulses cut by the period, ragged
+    small N."""
+    pk = spl.SPL_PASS_DENSE if pass_kind == "dense" else spl.SPL_PASS_STRUCTURED
+    px = np.concatenate([W.array_pixels(3, seed=41),
+                         W.pixel(256, 75.0, 30.0, 0.5, 9.5, 0.0), W.pixel(256, 75.0, 30.0, 0.2, 10.0, 0.5),
+                         W.pixel(256, 95.0, 30.0, 0.5, 0.5, 5.0), W.pixel(300, 130.0, 1.0, 1.5, 4.0, 2.0),
+                         W.pixel(300, 40.0, 99.0, 1.0, 6.0, 0.3),
+                         W.random_small(5, seed=42, n_min=20, n_max=300)])
+    out, off, reps = spl.batch_stationary(px, pass_kind=pk, flux_kind=spl.SPL_FLUX_BININT)
+    assert np.all(reps["status"] == 0), reps["status"]
+    o = out.cpu().numpy().astype(np.float64)
+    for k, p in enumerate(W.as_dicts(px)):
+        sh = int(p["shift_override"]) if int(p["shift_override"]) >= 0 else oracle.shift_l(p)
+        ref = oracle.stationary(p, tol=1e-12, shift=sh, flux="binint")
+        assert _l1(o[off[k]:off[k + 1]], ref) < L1_TOL, k
+    # the variant really differs from the point form where the pulse is narrow
+    pt, _, _ = spl.batch_stationary(px[3:5], pass_kind=pk)
+    assert _l1(pt.cpu().numpy(), o[off[3]:off[5]]) > 1e-2
 
 
 def test_batch_host_entry_point(spl):

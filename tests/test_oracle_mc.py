@@ -163,3 +163,13 @@ def test_mc_rejects_a_wrong_dead_time():
     wrong = oracle.stationary(W.as_dicts(W.pixel(N, 70.0, 30.0, 0.5, 6.0, 3.0))[0])
     with pytest.raises(AssertionError):
         _chi2_ok(h, h.sum() * wrong)
+
+
+def test_single_run_entry_matches_the_batch():
+    px = W.as_dicts(np.concatenate([W.pixel(64, 75.0, 30.0, 0.5, 3.0, 2.0), W.pixel(80, 95.0, 60.0, 1.0, 7.0, 1.0)]))
+    hist, off = oracle.mc_philox_histograms(px, 3, 500, seed=9)
+    for k, p in enumerate(px):
+        N = int(p["n_bins"])
+        for r in range(3):
+            np.testing.assert_array_equal(hist[3 * off[k] + r * N: 3 * off[k] + (r + 1) * N],
+                                          oracle.mc_philox_run(p, k, r, 500, seed=9))
