@@ -217,6 +217,7 @@ struct StopState {
     float rho, theta;     // current |lambda_2| and phase estimates (rho < 0: none yet)
     float err;            // last error bound
     float bmin, bmin_prev;  // smallest step of the current and the previous 8-step block
+    float tau;            // a priori bound on |lambda_2| (ergodicity coefficient), 1 if unknown
     int32_t k;            // steps taken
     int32_t reliable;     // 1 once a fit was made on steps well above FP32 noise
 };
@@ -258,7 +259,13 @@ constexpr float kBlockStall = 0.7f;
 // Outcomes of stop_update.
 enum : int { STOP_CONTINUE = 0, STOP_CONVERGED = 1, STOP_FLOOR = 2 };
 
-__host__ __device__ __forceinline__ void stop_init(StopState &s) {
+// tau: an upper bound on |lambda_2| known before the iteration (Dobrushin's
+// ergodicity coefficient, see batch_fused_kernel), or 1 when none is known.
+// Every modulus estimate is capped at it, and it replaces kRhoDefault while
+// no trustworthy fit exists.  With a bound tau < 1 the error estimate
+// delta_k tau / (1 - tau) is rigorous in exact arithmetic: zero-sum vectors
+// contract by tau in L1 at every step.
+__host__ __device__ __forceinline__ void stop_init(StopState &s, float tau = 1.f) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) s.delta[i] = 0.f;
     s.g11 = s.g12 = s.g22 = 0.f;
@@ -267,6 +274,7 @@ __host__ __device__ __forceinline__ void stop_init(StopState &s) {
     s.err = INFINITY;
     s.bmin = INFINITY;
     s.bmin_prev = INFINITY;
+    s.tau = tau;
     s.k = 0;
     s.reliable = 0;
 }
@@ -349,10 +357,10 @@ __host__ __device__ __forceinline__ int stop_update(StopState &s, float delta, f
             const float ratio = delta / prev;
             if (ratio < 1.f) ru = fmaxf(ru, ratio);
         }
-        ru = fminf(fmaxf(ru, 0.05f), 0.9999f);
+        ru = fminf(fmaxf(fminf(ru, s.tau), 0.05f), 0.9999f);
         if (s.theta >= 0.2f) W = min(8, max(2, (int)ceilf(6.2831853f / s.theta)));
     } else {
-        ru = kRhoDefault;
+        ru = fmaxf(fminf(kRhoDefault, s.tau), 0.05f);
     }
     W = min(W, k);
     float env = 0.f, pw = 1.f;

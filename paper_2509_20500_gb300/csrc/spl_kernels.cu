@@ -509,6 +509,22 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         }
         }
 
+        // ---- a priori bound on |lambda_2|: Dobrushin's ergodicity coefficient
+        // tau(P~) <= 1 - sum_j min_k P~_kj.  In p-space row k of P~ is
+        // w_j mu(k, j) / R_k, and R_k = 1 / rho_k = sum_{j >= k} w_j +
+        // e^-Lambda sum_{j < k} w_j never increases with k, so the column
+        // minimum is w_j min(rho_0, e^-Lambda rho_{j+1}) (rho_0 for the last
+        // column).  The roll J_l only permutes rows and leaves it unchanged.
+        __syncthreads();
+        float cmin = 0.f;
+        {
+            const float r0 = srho[0];
+            for (int j = tid; j < N; j += NT) cmin += gw[j] * (j + 1 < N ? fminf(r0, eL * srho[j + 1]) : r0);
+        }
+        // 1e-6 covers the FP32 rounding of the sum
+        const float tau = fminf(1.f, fmaxf(0.f, 1.f - block_sum<NT>(cmin, red)) + 1e-6f);
+        __syncthreads();   // every thread has read red[0] before it is reused
+
         // ---- start vector: uniform, normalised weights, softmax of logits,
         // or the learned start exp(z_{(j - c) mod N} + log lambda_j) / sum.
         float lsum = 0.f;
@@ -567,7 +583,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
 
         // ---- power iteration
         StopState st;
-        stop_init(st);
+        stop_init(st, tau);
         int status = ST_ENOCONV;
         // h_k = pi_{(k - l) mod N} * rho_k (J_l folded into the index) for the
         // first step; later steps get h from the statistics loop.

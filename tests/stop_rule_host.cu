@@ -9,10 +9,10 @@
 
 // Returns the step at which the rule ended (negative if it ended on an FP32
 // floor above the tolerance), 0 if it never did within K steps.
-extern "C" int stop_rule_replay(const double *d, int K, int M, float tol_err, int min_iter, float *err_out,
-                                float *rho_out, float *theta_out, int *reliable_out) {
+extern "C" int stop_rule_replay(const double *d, int K, int M, float tol_err, int min_iter, float tau,
+                                float *err_out, float *rho_out, float *theta_out, int *reliable_out) {
     spl::StopState s;
-    spl::stop_init(s);
+    spl::stop_init(s, tau);
     int stop = 0;
     for (int k = 0; k < K; ++k) {
         const double *dk = d + (size_t)k * M;

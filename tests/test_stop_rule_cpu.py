@@ -36,15 +36,15 @@ def rule(tmp_path_factory):
     lib = ctypes.CDLL(out)
     f = lib.stop_rule_replay
     f.restype = ctypes.c_int
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                   ctypes.POINTER(ctypes.c_int)]
 
-    def replay(d, min_iter=1):
+    def replay(d, min_iter=1, tau=1.0):
         d = np.ascontiguousarray(d, dtype=np.float64)
         err, rho, th, rel = ctypes.c_float(), ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
-        k = f(d.ctypes.data, d.shape[0], d.shape[1], TOL_ERR, min_iter, ctypes.byref(err), ctypes.byref(rho),
-              ctypes.byref(th), ctypes.byref(rel))
+        k = f(d.ctypes.data, d.shape[0], d.shape[1], TOL_ERR, min_iter, float(tau), ctypes.byref(err),
+              ctypes.byref(rho), ctypes.byref(th), ctypes.byref(rel))
         return k, dict(err=err.value, rho=rho.value, theta=th.value, reliable=rel.value)
     return replay
 
@@ -74,10 +74,13 @@ CLEAN = [(0.05, 0.0), (0.3, 0.0), (0.6, 0.0), (0.87, 0.0), (0.7, np.pi), (0.8, 0
 
 @pytest.mark.parametrize("rho,theta", CLEAN)
 @pytest.mark.parametrize("noise", [0.0, 1e-7])
-def test_transient_from_far_start(rule, rho, theta, noise):
+@pytest.mark.parametrize("tau_margin", [None, 0.02])
+def test_transient_from_far_start(rule, rho, theta, noise, tau_margin):
+    """tau_margin None: no a priori bound (tau = 1); else an honest bound
+    tau = |lambda_2| + margin, as the ergodicity coefficient gives."""
     rng = np.random.default_rng(int(rho * 100 + theta * 10 + noise * 1e9))
     d, true = sequence(rng, 200, 1.0, rho, theta, noise, amp2=0.5)
-    k, st = rule(d)
+    k, st = rule(d, tau=1.0 if tau_margin is None else rho + tau_margin)
     assert k > 0, st
     assert true[k] < TOL, (k, true[k], st)
     # no more than a few steps past the first iterate within tol_err (more
@@ -125,13 +128,32 @@ def test_floor_above_tolerance_ends_as_not_converged(rule, noise):
 def test_warm_start_on_a_slow_mode(rule, rho, theta, amp, noise):
     """A warm start whose whole error lies in a slow mode: its steps are
     already below the stall floors, so only the decay pattern tells it from
-    noise; the rule must not stop while the error exceeds the tolerance."""
+    noise; the rule must not stop while the error exceeds the tolerance,
+    with or without an honest a priori bound on |lambda_2|."""
     for seed in range(5):
-        rng = np.random.default_rng(seed)
-        d, true = sequence(rng, 300, amp, rho, theta, noise)
-        k, st = rule(d)
-        assert k > 0, st
-        assert true[k] < TOL, (seed, k, true[k], st)
+        for tau in (1.0, min(1.0, rho + 0.03)):
+            rng = np.random.default_rng(seed)
+            d, true = sequence(rng, 300, amp, rho, theta, noise)
+            k, st = rule(d, tau=tau)
+            assert k > 0, st
+            assert true[k] < TOL, (seed, tau, k, true[k], st)
+
+
+@pytest.mark.parametrize("rho_fast,tau", [(0.005, 0.17), (0.01, 0.45), (0.02, 0.8)])
+@pytest.mark.parametrize("noise", [5e-8, 7e-8, 1.2e-7])
+def test_a_priori_bound_ends_a_fast_start_on_the_floor(rule, rho_fast, tau, noise):
+    """A good warm start on a fast-mixing chain: one step lands on the FP32
+    floor, where no trustworthy fit is possible.  Without an a priori bound
+    the rule must assume |lambda_2| = 0.9 and wait for a stall; with the
+    ergodicity bound tau it stops as soon as the floor is reached, with the
+    true error below the tolerance."""
+    rng = np.random.default_rng(int(tau * 100 + noise * 1e9))
+    d, true = sequence(rng, 60, 8e-4, rho_fast, 0.0, noise)
+    k_blind, _ = rule(d)
+    k, st = rule(d, tau=tau)
+    assert 0 < k <= 4, (k, st)
+    assert k <= k_blind
+    assert true[k] < TOL
 
 
 def test_min_iter_is_respected(rule):
