@@ -336,6 +336,16 @@ __host__ __device__ __forceinline__ int stop_update(StopState &s, float delta, f
     s.g22 = s.g11;
     s.g12 = d1;
     s.g11 = dd;
+    // With an a priori contraction bound the error of this iterate is at most
+    // delta tau / (1 - tau) (the sum of all later steps, each at most tau
+    // times the one before): no fit and no minimum step count needed.
+    if (s.tau < 1.f && k >= min_iter) {
+        const float rig = delta * s.tau / (1.f - s.tau);
+        if (rig < tol_err) {
+            s.err = rig;
+            return STOP_CONVERGED;
+        }
+    }
     s.bmin = fminf(s.bmin, delta);
     int floor_long = STOP_CONTINUE;
     if (k % kBlock == 0) {

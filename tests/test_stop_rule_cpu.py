@@ -177,3 +177,61 @@ def test_lambda2_estimate_from_clean_transient(rule):
         assert st["reliable"] == 1
         assert abs(st["rho"] - rho) < 2e-2 * rho, (rho, theta, st)
         assert abs(st["theta"] - theta) < 5e-2, (rho, theta, st)
+
+
+def _column_min_bound(P):
+    return 1.0 - P.min(axis=0).sum()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ergodicity_bound_on_real_chains(seed):
+    """On P~ of Eq. 6 (oracle build, broad random pixels): |lambda_2| <=
+    tau_1 (Dobrushin's coefficient, max over row pairs of half the L1
+    distance) <= 1 - sum_j min_i P~_ij, the bound the batch kernel forms in
+    closed form."""
+    import oracle
+    from paper_2509_20500_gb300 import workloads as W
+    for p in W.as_dicts(W.random_small(4, seed=100 + seed, n_min=20, n_max=120)):
+        P = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+        tau1 = max(0.5 * np.abs(P - P[i]).sum(axis=1).max() for i in range(P.shape[0]))
+        lam = np.sort(np.abs(np.linalg.eigvals(P)))[::-1]
+        assert lam[1] <= tau1 + 1e-12
+        assert tau1 <= _column_min_bound(P) + 1e-12
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("noise", [0.0, 5e-8])
+def test_rigorous_stop_on_real_chains(rule, seed, noise):
+    """Power iteration on real chains, from the uniform vector and from warm
+    starts at distances 1e-3 .. 1e-7, replayed through the rule with the
+    column-minimum bound as tau: every stop has true L1 error below the
+    tolerance, also with a rounding floor injected into every iterate."""
+    import oracle
+    from paper_2509_20500_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    for p in W.as_dicts(W.random_small(3, seed=200 + seed, n_min=30, n_max=160)):
+        P = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+        N = P.shape[0]
+        pi_star = oracle.power(P, tol=1e-15)[0]
+        tau = _column_min_bound(P)
+        for amp in (None, 1e-3, 1e-5, 1e-7):
+            if amp is None:
+                pi = np.full(N, 1.0 / N)
+            else:
+                x = rng.standard_normal(N)
+                x -= x.mean()
+                pi = np.maximum(pi_star + amp * x / np.abs(x).sum(), 0.0)
+                pi /= pi.sum()
+            ds, true = [], []
+            for _ in range(400):
+                y = pi @ P
+                if noise:
+                    y = y * (1.0 + noise * rng.standard_normal(N))
+                y /= y.sum()
+                ds.append(y - pi)
+                pi = y
+                true.append(np.abs(pi - pi_star).sum())
+            k, st = rule(np.array(ds), tau=min(1.0, tau + 1e-6))
+            assert k != 0, (p, amp, st)
+            if k > 0:
+                assert true[k - 1] < TOL, (p, amp, k, true[k - 1], tau, st)
