@@ -448,7 +448,7 @@ def run_gpu(args):
     # 21 x 21 grid over [0, 10]^2 at 256 bins, 25 runs x 50,000 cycles each
     if not args.no_mc and rank == 0:
         g = W.accuracy_grid()
-        runs, cycles, nb = 25, 50000, 256
+        runs, cycles, nb = 25, args.mc_cycles, 256
         spl.mc_histograms(g[:4], 2, 1000, seed=1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -587,6 +587,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-spectral", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--mc-cycles", type=int, default=50000, help="laser cycles per Monte Carlo run")
     ap.add_argument("--audit", type=int, default=64, help="pixels of the timed output checked against the oracle")
     ap.add_argument("--train-pixels", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=60)
