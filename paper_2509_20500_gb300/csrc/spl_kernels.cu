@@ -147,8 +147,9 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // coalesced and, inside the span, 32-entry block cb is "near" for columns
 // c > cb, "far" for c < cb, and needs a per-entry select only for c == cb.
 // b runs over [b_lo, b_hi); v is indexed by b (callers offset the pointer
-// for a chunk).  All bounds are multiples of 4; the span lies either fully
-// inside [b_lo, b_hi) or fully outside it.
+// for a chunk).  All bounds are multiples of 4; the span either starts at or
+// after b_lo, or lies fully below it; a span reaching past b_hi is cut at a
+// 32-entry block boundary (b_hi a multiple of 32 then).
 template <int C, bool kRowPass>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
@@ -164,7 +165,7 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         tri_run<C>(v, b_lo, min(b_hi, base), m, acc, comp);
     }
     // the span itself (32 C entries, added as chunks of at most kChain)
-    if (base >= b_lo && span_end <= b_hi) {
+    if (base >= b_lo && base < b_hi) {
         const float4 *v4 = reinterpret_cast<const float4 *>(v);
         float in[kNch][C];
         chains_zero<C>(in);
@@ -177,8 +178,9 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
                 const bool near = kRowPass ? (c < cb) : (c > cb);
                 m[c] = near ? mlo[c] : mhi[c];
             }
+            // blocks past b_hi (only where the span is cut) add nothing
 #pragma unroll 2
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < (base + 32 * cb < b_hi ? 8 : 0); ++q) {
                 const float4 x = v4[((base + 32 * cb) >> 2) + q];
                 const int t = 4 * q;   // offset of x.x inside the block
 #pragma unroll
@@ -458,6 +460,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         const int N = p.N, l = p.l;
         const int64_t off = a.offsets ? a.offsets[p.index] : p.out_off;
         const int npad = pad_len(N, C);
+        const int nrow = (N + 31) & ~31;         // rows a pass reads (v is zero in [N, npad))
         const int span = NT * C;                 // outputs per group
         const int ngroups = (N + span - 1) / span;
 
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                     mlo[c] = u;
                     mhi[c] = u * eL;
                 }
-                tri_pass<C, true>(sv, 0, npad, base, lane, mlo, mhi, r);
+                tri_pass<C, true>(sv, 0, nrow, base, lane, mlo, mhi, r);
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const int k = base + 32 * c + lane;
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                         mlo[c] = w;
                         mhi[c] = w * eL;
                     }
-                    tri_pass<C, false>(sv, 0, npad, base, lane, mlo, mhi, y);
+                    tri_pass<C, false>(sv, 0, nrow, base, lane, mlo, mhi, y);
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
                         const int j = base + 32 * c + lane;
