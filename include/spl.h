@@ -282,6 +282,12 @@ SPL_API int64_t spl_mlp_param_count(void);
 SPL_API spl_status_t spl_mlp_set_params(spl_mlp_t *m, const float *h_params, int64_t count);
 SPL_API spl_status_t spl_mlp_get_params(spl_mlp_t *m, float *h_params, int64_t count);
 SPL_API spl_status_t spl_mlp_forward(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, float *d_logits);
+/* Device time of the forward pass alone: uploads the pixels once, then times
+ * `reps` forward passes (features and the five GEMMs, logits kept inside the
+ * network) with CUDA events on the network's stream; *ms_per_forward gets the
+ * mean.  Synchronises the stream. */
+SPL_API spl_status_t spl_mlp_time_forward(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, int32_t reps,
+                                          float *ms_per_forward);
 SPL_API spl_status_t spl_mlp_loss_grad(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, const float *d_target,
                                        float *h_loss, float *h_grads);
 SPL_API spl_status_t spl_mlp_train_step(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, const float *d_target,

@@ -46,6 +46,10 @@ constexpr uint32_t kTileBytes = BM * BK * 2;          // 16 KB (A or B tile)
 constexpr uint32_t kStageBytes = 2 * kTileBytes;
 constexpr uint32_t kTmemCols = BN;
 constexpr size_t kGemmSmem = (size_t)STAGES * kStageBytes + 1024;
+// 8 warps: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs, and
+// all eight run the epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
+// lane quadrant a warp may access) and accumulator columns 64 (w / 4) .. + 63.
+constexpr int kGemmThreads = 256;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 enum : int { EPI_GELU = 0, EPI_LOGITS = 1, EPI_DGELU = 2, EPI_F32 = 3 };
@@ -70,17 +74,21 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 
 // D[M x N] = A[M x K] * B[N x K]^T, both operands K-major BF16.
 template <int MODE>
-__global__ void __launch_bounds__(128, 2) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
-                                                          const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads, 2) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                   const __grid_constant__ CUtensorMap tb, GemmArgs g) {
     extern __shared__ uint8_t gemm_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[STAGES];
     __shared__ __align__(8) uint64_t empty_bar[STAGES];
     __shared__ __align__(8) uint64_t acc_bar;
     __shared__ uint32_t tmem_base;
+    __shared__ float s_bias[BN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int KB = g.K / BK;
+    if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
+        for (int c = threadIdx.x; c < BN; c += kGemmThreads) s_bias[c] = (n0 + c < g.N) ? g.bias[n0 + c] : 0.f;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -139,17 +147,19 @@ __global__ void __launch_bounds__(128, 2) gemm_bf16_kernel(const __grid_constant
     }
     __syncwarp();
 
-    // Epilogue: warp w owns accumulator rows 32 w .. 32 w + 31 (TMEM lanes).
+    // Epilogue: warp w owns accumulator rows 32 (w % 4) .. + 31 (TMEM lanes)
+    // and columns 64 (w / 4) .. + 63.
     const bool acc_ok = umma::mbar_wait(&acc_bar, 0, kWaitLimit);
     umma::tc_fence_after();
     if (!ok || !acc_ok) {
         if (g.err_flag) atomicExch(g.err_flag, 1);
     } else {
-        const int row = m0 + warp * 32 + lane;
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = m0 + quad * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             uint32_t r[32];
-            umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            umma::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
             umma::tmem_ld_wait();
             const int nb = n0 + c0;
             if (nb >= g.N) continue;
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(128, 2) gemm_bf16_kernel(const __grid_constant
             for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
             if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) v[c] += (nb + c < g.N) ? __ldg(g.bias + nb + c) : 0.f;
+                for (int c = 0; c < 32; ++c) v[c] += s_bias[c0 + c];
             }
             if (MODE == EPI_GELU) {
                 if (g.out_pre) {
@@ -397,7 +407,7 @@ cudaError_t launch_gemm_mode(const CUtensorMap &ta, const CUtensorMap &tb, const
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     if (e != cudaSuccess) return e;
     dim3 grid(g.M / BM, (g.N + BN - 1) / BN);
-    k<<<grid, 128, kGemmSmem, s>>>(ta, tb, g);
+    k<<<grid, kGemmThreads, kGemmSmem, s>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -713,6 +723,31 @@ extern "C" spl_status_t spl_mlp_forward(spl_mlp_t *m, const spl_pixel_t *h_px, i
     if (d_logits)
         MCU(cudaMemcpyAsync(d_logits, m->logits, sizeof(float) * (size_t)n * kOutPad, cudaMemcpyDeviceToDevice,
                             m->stream));
+    return read_err(m);
+}
+
+extern "C" spl_status_t spl_mlp_time_forward(spl_mlp_t *m, const spl_pixel_t *h_px, int32_t n, int32_t reps,
+                                             float *ms_per_forward) {
+    if (!ms_per_forward || reps < 1) return SPL_EINVAL;
+    spl_status_t st = check_batch(m, h_px, n);
+    if (st != SPL_OK) return st;
+    MCU(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+    if ((st = upload_pixels(m, h_px, n)) != SPL_OK) return st;
+    if ((st = forward(m, n, false)) != SPL_OK) return st;   // warm-up
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MCU(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, m->stream);
+    for (int32_t r = 0; r < reps && e == cudaSuccess && st == SPL_OK; ++r) st = forward(m, n, false);
+    if (e == cudaSuccess && st == SPL_OK) e = cudaEventRecord(e1, m->stream);
+    if (e == cudaSuccess && st == SPL_OK) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess && st == SPL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != SPL_OK) return st;
+    if (e != cudaSuccess) return mfail(e, "time forward");
+    *ms_per_forward = ms / (float)reps;
     return read_err(m);
 }
 

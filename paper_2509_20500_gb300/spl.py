@@ -56,7 +56,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
-            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms"]
+            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward"]
 
 _lib = None
 _lock = threading.Lock()
@@ -124,6 +124,8 @@ def lib():
         L.spl_mlp_get_params.restype = ctypes.c_int
         L.spl_mlp_forward.argtypes = [vp, P, i32, vp]
         L.spl_mlp_forward.restype = ctypes.c_int
+        L.spl_mlp_time_forward.argtypes = [vp, P, i32, i32, fp]
+        L.spl_mlp_time_forward.restype = ctypes.c_int
         L.spl_mlp_loss_grad.argtypes = [vp, P, i32, vp, fp, vp]
         L.spl_mlp_loss_grad.restype = ctypes.c_int
         L.spl_mlp_train_step.argtypes = [vp, P, i32, vp, ctypes.c_float, ctypes.c_float, fp]
@@ -380,6 +382,13 @@ class MLP:
     def set_params(self, p: np.ndarray):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(lib().spl_mlp_set_params(self._m, ctypes.c_void_p(p.ctypes.data), p.size), "spl_mlp_set_params")
+
+    def time_forward(self, px: np.ndarray, reps: int = 10) -> float:
+        """Device ms of one forward pass (kernels only) over px."""
+        ms = ctypes.c_float()
+        _check(lib().spl_mlp_time_forward(self._m, pixels_to_c(px), len(px), int(reps), ctypes.byref(ms)),
+               "spl_mlp_time_forward")
+        return float(ms.value)
 
     def forward(self, px: np.ndarray, out=None):
         import torch
