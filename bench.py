@@ -254,7 +254,7 @@ def run_gpu(args):
     total = int(off[-1])
     out = torch.empty(total, dtype=torch.float32, device=dev)
     d_off = torch.from_numpy(off).to(dev)
-    c_px = spl.pixels_to_c(px)
+    c_px = spl.pixels_to_c(px, pinned=True)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 

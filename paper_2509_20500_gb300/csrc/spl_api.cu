@@ -66,7 +66,8 @@ spl_status_t make_pixel(const spl_pixel_t &p, PixelDev &d) {
     if (p.shift_override >= 0) {
         l = p.shift_override;
     } else {
-        const volatile double x_d = std::fmod(p.t_d, p.t_r);
+        // fmod is exact and returns t_d itself when 0 <= t_d < t_r
+        const volatile double x_d = p.t_d < p.t_r ? p.t_d : std::fmod(p.t_d, p.t_r);
         const volatile double num = x_d * (double)N;
         const double q = num / p.t_r;
         l = (int64_t)std::ceil(q);
@@ -492,6 +493,8 @@ struct BatchWorkspace {
     size_t h_px_cap = 0;
     ReportDev *h_reps = nullptr;     // pinned
     size_t h_reps_cap = 0;
+    std::vector<int32_t> order;      // host scratch of make_work_list, kept across calls
+    std::vector<int64_t> offs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
 };
@@ -541,12 +544,21 @@ spl_status_t status_of_alloc(cudaError_t e, const char *what) {
 spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int32_t n, int *nmax_out) {
     cudaError_t e = grow_host(&ws.h_px, &ws.h_px_cap, (size_t)n);
     if (e != cudaSuccess) return status_of_alloc(e, "pinned work list");
-    std::vector<int32_t> order((size_t)n);
+    std::vector<int32_t> &order = ws.order;
+    std::vector<int64_t> &off = ws.offs;
+    order.resize((size_t)n);
+    off.resize((size_t)n + 1);
+    off[0] = 0;
+    bool uniform = true;
+    for (int32_t k = 0; k < n; ++k) {
+        off[k + 1] = off[k] + h_pixels[k].n_bins;
+        uniform = uniform && h_pixels[k].n_bins == h_pixels[0].n_bins;
+    }
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return h_pixels[a].n_bins > h_pixels[b].n_bins; });
-    std::vector<int64_t> off((size_t)n + 1, 0);
-    for (int32_t k = 0; k < n; ++k) off[k + 1] = off[k] + h_pixels[k].n_bins;
+    // largest pixels first; a batch of one size is already in that order
+    if (!uniform)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return h_pixels[a].n_bins > h_pixels[b].n_bins; });
     int nmax = 2;
     for (int32_t r = 0; r < n; ++r) {
         const int32_t k = order[r];

@@ -172,10 +172,20 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def pixels_to_c(px: np.ndarray):
-    """Marshal a workloads.PIXEL_DTYPE array into a ctypes spl_pixel_t array."""
+def pixels_to_c(px: np.ndarray, pinned: bool = False):
+    """Marshal a workloads.PIXEL_DTYPE array into a ctypes spl_pixel_t array.
+    pinned=True places it in page-locked host memory (through PyTorch), so the
+    library's host-to-device copies of it are asynchronous; the array keeps
+    its buffer alive."""
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
-    arr = (spl_pixel_t * max(1, len(px)))()
+    n = max(1, len(px))
+    if pinned:
+        import torch
+        buf = torch.empty(n * ctypes.sizeof(spl_pixel_t), dtype=torch.uint8, pin_memory=True)
+        arr = (spl_pixel_t * n).from_address(buf.data_ptr())
+        arr._pinned_buffer = buf
+    else:
+        arr = (spl_pixel_t * n)()
     ctypes.memmove(arr, px.ctypes.data, px.nbytes)
     return arr
 
