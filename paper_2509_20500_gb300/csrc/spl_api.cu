@@ -484,6 +484,8 @@ struct BatchWorkspace {
     size_t scratch_cap = 0;
     int *counter = nullptr;
     size_t counter_cap = 0;
+    PixelConst *pconst = nullptr;
+    size_t pconst_cap = 0;
     // staging of the host-buffer entry point
     float *d_warm = nullptr, *d_out = nullptr;
     size_t warm_cap = 0, out_cap = 0;
@@ -595,6 +597,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
     if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
     if ((e = grow(&ws.counter, &ws.counter_cap, 1)) != cudaSuccess) return status_of_alloc(e, "counter");
+    if ((e = grow(&ws.pconst, &ws.pconst_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "constants");
     const size_t per_block = level == 2 ? 0 : (size_t)(level == 1 ? 5 : 7) * npad;
     if (per_block && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * per_block)) != cudaSuccess)
         return status_of_alloc(e, "scratch");
@@ -618,6 +621,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.min_iter = std::max(1, min_iter);
     a.structured = structured;
     a.flux_kind = flux_kind;
+    a.pconst = ws.pconst;
     if (time_kernel) {
         if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
@@ -740,8 +744,10 @@ extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t 
     if (nmax > 4096) return SPL_EINVAL;
     cudaError_t e;
     if ((e = grow(&ws->px, &ws->px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
+    if ((e = grow(&ws->pconst, &ws->pconst_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "constants");
     SPL_CU(cudaMemcpyAsync(ws->px, ws->h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
     SpectralArgs a{};
+    a.pconst = ws->pconst;
     a.px = ws->px;
     a.n = n;
     a.npad_max = batch_pad_len(nmax);

@@ -31,6 +31,22 @@ struct PixelDev {
     int32_t pad_;
 };
 
+// Per-pixel constants of the batch flux phase (K1), formed once per pixel by
+// pixel_const_kernel (one thread per pixel) and read by every thread of the
+// block that takes the pixel.  They are FP64 transcendentals and quotients;
+// this GPU runs FP64 at 1/64 of the FP32 rate, so forming them in every
+// thread of a block cost as much as a dense pass.
+struct PixelConst {
+    double Phi0, Lambda, gnorm, delta, beta, inv_sigma, bg;
+    double bgK_lo, bgK_hi;   // bg exp(Lambda/2 - S G) left / right of the pulse (G = -Phi0, 1 - Phi0)
+    double half_z;           // Delta / (2 sigma)
+    double tail_ratio;       // 2 sinh(beta/2) / beta (1 if beta = 0): bin-integrated / point tail weight
+    double g0, q1, q64;      // exp(-beta/2), exp(-beta), exp(-64 beta): the geometric factor tables
+    float bg_f, uK_lo, uK_hi, eL;   // uK: tail row factors exp(S G - Lambda/2) for B = 0; eL = exp(-Lambda)
+    int32_t j_lo, j_hi;      // bins with |z| <= 9 (the pulse); the rest are tail bins
+    int32_t pad0_, pad1_;
+};
+
 // Per-pixel result record written by the kernels (mirrors spl_report_t).
 struct ReportDev {
     int32_t iters;
@@ -70,6 +86,75 @@ __device__ __forceinline__ FluxConst flux_const(const PixelDev &p) {
     c.gnorm = 0.39894228040143267794 / p.sigma;
     c.delta = p.t_r / (double)p.N;
     return c;
+}
+
+// The constants above for one pixel (FP64).  Outside the pulse (|z| > 9)
+// exp(Lambda/2 - F_j) splits into exp(Lambda/2 - S G) with G one of two
+// constants, times exp(-B (j + 1/2) / N), a geometric sequence.
+__device__ __forceinline__ void pixel_const(const PixelDev &p, PixelConst &c) {
+    const FluxConst fc = flux_const(p);
+    c.Phi0 = fc.Phi0;
+    c.Lambda = fc.Lambda;
+    c.gnorm = fc.gnorm;
+    c.delta = fc.delta;
+    c.beta = p.B / (double)p.N;
+    c.inv_sigma = 1.0 / p.sigma;
+    c.bg = p.B / p.t_r;
+    c.bgK_lo = c.bg * exp(0.5 * fc.Lambda + p.S * fc.Phi0);
+    c.bgK_hi = c.bg * exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));
+    c.half_z = 0.5 * fc.delta * c.inv_sigma;
+    c.tail_ratio = c.beta > 0.0 ? 2.0 * sinh(0.5 * c.beta) / c.beta : 1.0;
+    c.g0 = exp(-0.5 * c.beta);
+    c.q1 = exp(-c.beta);
+    c.q64 = exp(-64.0 * c.beta);
+    c.bg_f = (float)c.bg;
+    c.uK_lo = (float)exp(-0.5 * fc.Lambda - p.S * fc.Phi0);
+    c.uK_hi = (float)exp(p.S * (1.0 - fc.Phi0) - 0.5 * fc.Lambda);
+    c.eL = (float)exp(-fc.Lambda);
+    // pulse bins: s_j within 9 sigma of tau, j in [(tau - 9 sigma)/Delta - 1/2, (tau + 9 sigma)/Delta - 1/2]
+    const double lo = (p.tau - kTailZ * p.sigma) / fc.delta - 0.5;
+    const double hi = (p.tau + kTailZ * p.sigma) / fc.delta - 0.5;
+    c.j_lo = lo < 0.0 ? 0 : (int)ceil(lo);
+    c.j_hi = hi >= (double)(p.N - 1) ? p.N - 1 : (int)floor(hi);
+    c.pad0_ = c.pad1_ = 0;
+}
+
+// x^e for an integer e >= 0 by repeated squaring (FP64 products only).
+__host__ __device__ __forceinline__ double pow_uint(double x, int e) {
+    double r = 1.0;
+    while (e > 0) {
+        if (e & 1) r *= x;
+        x *= x;
+        e >>= 1;
+    }
+    return r;
+}
+
+// exp(x) for |x| <= 700 in FP64 operations only: x = n ln 2 + r with n the
+// nearest integer to x / ln 2 and |r| <= ln(2)/2 (one fused multiply-add, so
+// the only error of r is that of the rounded ln 2 times n, about
+// n 2.7e-17), then e^r by its Taylor series to degree 10 (remainder below
+// 3e-13 relative) and 2^n exactly.  About 14 FP64 operations against about
+// twice that for a general-purpose exp; accurate to about 1e-12 relative
+// over the arguments the flux factors use (|x| <= 125).
+__host__ __device__ __forceinline__ double exp_series(double x) {
+    constexpr double kLn2 = 0.69314718055994530942;
+    constexpr double kInvLn2 = 1.44269504088896340736;
+    const double n = rint(x * kInvLn2);
+    const double r = fma(-n, kLn2, x);
+    // 1/k! for k = 10 .. 0, Horner
+    double q = 1.0 / 3628800.0;
+    q = fma(q, r, 1.0 / 362880.0);
+    q = fma(q, r, 1.0 / 40320.0);
+    q = fma(q, r, 1.0 / 5040.0);
+    q = fma(q, r, 1.0 / 720.0);
+    q = fma(q, r, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    q = fma(q, r, 1.0);
+    q = fma(q, r, 1.0);
+    return ldexp(q, (int)n);
 }
 
 // Eq. 1 flux lambda(s_j) and Theorem 1's F(s_j) = S [Phi(z_j) - Phi(z_0)] + B s_j / t_r.
@@ -280,32 +365,37 @@ __host__ __device__ __forceinline__ void stop_init(StopState &s, float tau = 1.f
 }
 
 // Fit of the 2-term recurrence from the Gram data; returns false if degenerate.
+// FP32 throughout: the Gram sums are FP32 already, and the only cancellation
+// (det of nearly collinear steps) is routed to the single-mode ratio while
+// det / (g11 g22) is still above 1e-3, where FP32 keeps about four digits of
+// det; every thread of a block runs this once per step, so the FP64 pipe
+// (1/64 of the FP32 rate on this GPU) is kept out of it.
 __host__ __device__ __forceinline__ bool fit_lambda2(float g11, float g12, float g22, float h1, float h2,
                                             float &rho, float &theta) {
     if (!(g11 > 0.f) || !(g22 > 0.f)) return false;
-    const double G11 = g11, G12 = g12, G22 = g22, H1 = h1, H2 = h2;
-    const double det = G11 * G22 - G12 * G12;
-    double a, b;
+    const float det = fmaf(g11, g22, -g12 * g12);
+    float a, b;
     // Nearly collinear steps (one real mode dominates, or two close real
     // modes the FP32 Gram data cannot separate): single-mode ratio.
-    if (det <= 1e-3 * G11 * G22) {
-        a = H1 / G11;
-        rho = (float)fabs(a);
-        theta = a >= 0.0 ? 0.f : 3.14159265358979f;
+    if (det <= 1e-3f * g11 * g22) {
+        a = h1 / g11;
+        rho = fabsf(a);
+        theta = a >= 0.f ? 0.f : 3.14159265358979f;
         return true;
     }
-    a = (H1 * G22 - H2 * G12) / det;
-    b = (G11 * H2 - G12 * H1) / det;
-    const double disc = a * a + 4.0 * b;
-    if (disc < 0.0) {
-        rho = (float)sqrt(-b);
-        theta = (float)atan2(sqrt(-disc), a);
+    const float inv = 1.f / det;
+    a = (h1 * g22 - h2 * g12) * inv;
+    b = (g11 * h2 - g12 * h1) * inv;
+    const float disc = fmaf(a, a, 4.f * b);
+    if (disc < 0.f) {
+        rho = sqrtf(-b);
+        theta = atan2f(sqrtf(-disc), a);
     } else {
-        const double sq = sqrt(disc);
-        const double r1 = 0.5 * (a + sq), r2 = 0.5 * (a - sq);
-        const double r = fabs(r1) >= fabs(r2) ? r1 : r2;
-        rho = (float)fabs(r);
-        theta = r >= 0.0 ? 0.f : 3.14159265358979f;
+        const float sq = sqrtf(disc);
+        const float r1 = 0.5f * (a + sq), r2 = 0.5f * (a - sq);
+        const float r = fabsf(r1) >= fabsf(r2) ? r1 : r2;
+        rho = fabsf(r);
+        theta = r >= 0.f ? 0.f : 3.14159265358979f;
     }
     return true;
 }

@@ -29,13 +29,19 @@ namespace spl {
 // b < base, the 32C-wide band and an "above" region b >= base + 32C; only
 // the band needs a per-entry select.  Every entry costs one FFMA:
 // acc_c += v_b * m_c(b) with the regenerated factor m_c(b).  Sums are
-// blocked: 128-term inner chains added into an outer accumulator.
+// blocked: four interleaved FFMA chains over a kChain-row chunk, whose sum
+// is added into a compensated outer accumulator.
 
 // Tuning knobs of the dense passes (compile-time): chunk length of the
 // compensated sums, FFMA chains per output, outputs per thread in the batch
 // kernel and its target blocks per SM.
+// 64-row chunks: within a chunk every FMA rounds a chain's running sum, so
+// the terms that follow a large one (the tails of a concentrated h after the
+// pulse rows) each cost half an ulp of that large sum.  Restarting the chains
+// every 64 rows keeps the FP32 fixed point of bright narrow pulses within
+// about 1e-7 L1 of the exact pmf (256-row chunks: up to 1.1e-6).
 #ifndef SPL_KCHAIN
-#define SPL_KCHAIN 256
+#define SPL_KCHAIN 64
 #endif
 #ifndef SPL_NCH
 #define SPL_NCH 4
@@ -53,6 +59,16 @@ namespace spl {
 #endif
 constexpr int kChain = SPL_KCHAIN;
 constexpr int kNch = SPL_NCH;
+
+// Compensated accumulation of a chunk sum x into (acc, comp) by Dekker's
+// Fast2Sum: the rounding error of acc + x is x - (s - acc), exact while
+// |acc| >= |x| (the usual case once a few chunks are in; otherwise a close
+// estimate), three operations instead of TwoSum's six.
+__device__ __forceinline__ void fast_two_sum_acc(float &acc, float &comp, float x) {
+    const float s = acc + x;
+    comp += x - (s - acc);
+    acc = s;
+}
 
 // Compensated accumulation of a positive chunk sum x into (acc, comp):
 // TwoSum gives the exact rounding error of acc + x, which is carried in comp.
@@ -80,7 +96,7 @@ __device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[
         if (kNch == 4) t = (in[0][c] + in[1][c]) + (in[2][c] + in[3][c]);
         else if (kNch == 2) t = in[0][c] + in[1][c];
         else t = in[0][c];
-        two_sum_acc(acc[c], comp[c], t);
+        fast_two_sum_acc(acc[c], comp[c], t);
     }
 }
 
@@ -115,7 +131,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         }
 #pragma unroll
         for (int c = 0; c < C; ++c)
-            two_sum_acc(acc[c], comp[c], (in01[c].x + in01[c].y) + (in23[c].x + in23[c].y));
+            fast_two_sum_acc(acc[c], comp[c], (in01[c].x + in01[c].y) + (in23[c].x + in23[c].y));
     }
 #else
     for (int b0 = lo; b0 < hi; b0 += kChain) {
@@ -304,17 +320,27 @@ __device__ float block_scan(const float *v, float *out, int n, bool rev, float *
 // where the second factor is a geometric sequence taken from two FP64
 // tables (64 j-steps and 64-j blocks), so outside the pulse (|z| > 9, where
 // G_j is one of two constants) a bin costs two FP64 products instead of an
-// FP64 exp; inside the pulse the first factor is an FP64 exp of its own.
-struct BatchFlux {
-    double Phi0, Lambda, gnorm, delta, beta, inv_sigma, bg;
-    double bgK_lo, bgK_hi;   // bg * exp(Lambda/2 - S G) on either side of the pulse
-    double K_half;           // exp(Lambda/2)
-    float bg_f;
-    float uK_lo, uK_hi;      // tail row factors exp(S G - Lambda/2) for B = 0 (where g = 1 and w = 0)
-    int j_lo, j_hi;          // bins with |z| <= 9 (the pulse); the rest are tail bins
-    double half_z;           // Delta / (2 sigma)
-    double tail_ratio;       // bin-integrated / point column factor outside the pulse, 2 sinh(beta/2) / beta
-};
+// FP64 exp; inside the pulse G_j needs an FP64 erfc and the two exponentials
+// come from exp_series.  The per-pixel constants (PixelConst) come from
+// pixel_const_kernel.
+
+// One thread per pixel: the constants of the work list's pixels.
+__global__ void __launch_bounds__(128) pixel_const_kernel(const PixelDev *__restrict__ px, int n,
+                                                          PixelConst *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    PixelConst c;
+    pixel_const(px[k], c);
+    out[k] = c;
+}
+
+// Fills the geometric tables of one pixel: t_lo[b] = exp(-beta (b + 1/2)),
+// t_hi[a] = exp(-64 beta a), by FP64 products from the pixel's constants.
+template <int NT>
+__device__ __forceinline__ void fill_geo_tables(const PixelConst &c, double *t_lo, double *t_hi, int nblk) {
+    for (int b = threadIdx.x; b < 64; b += NT) t_lo[b] = c.g0 * pow_uint(c.q1, b);
+    for (int a = threadIdx.x; a < nblk; a += NT) t_hi[a] = pow_uint(c.q64, a);
+}
 
 // Phi(b) - Phi(a) for a <= b, from the side of the distribution where both
 // tails are small, so a narrow interval far out keeps its relative accuracy.
@@ -326,36 +352,9 @@ __device__ __forceinline__ double cdf_diff(double a, double b) {
 }
 
 
-__device__ __forceinline__ void batch_flux_setup(const PixelDev &p, BatchFlux &f, double *t_lo, double *t_hi,
-                                                 int nblk) {
-    const FluxConst fc = flux_const(p);
-    f.Phi0 = fc.Phi0;
-    f.Lambda = fc.Lambda;
-    f.gnorm = fc.gnorm;
-    f.delta = fc.delta;
-    f.beta = p.B / (double)p.N;
-    f.inv_sigma = 1.0 / p.sigma;
-    f.bg = p.B / p.t_r;
-    f.bg_f = (float)f.bg;
-    f.bgK_lo = f.bg * exp(0.5 * fc.Lambda + p.S * fc.Phi0);             // G = -Phi0 (left of the pulse)
-    f.bgK_hi = f.bg * exp(0.5 * fc.Lambda - p.S * (1.0 - fc.Phi0));     // G = 1 - Phi0 (right of the pulse)
-    f.K_half = exp(0.5 * fc.Lambda);
-    f.uK_lo = (float)exp(-0.5 * fc.Lambda - p.S * fc.Phi0);
-    f.uK_hi = (float)exp(p.S * (1.0 - fc.Phi0) - 0.5 * fc.Lambda);
-    f.half_z = 0.5 * fc.delta / p.sigma;
-    f.tail_ratio = f.beta > 0.0 ? 2.0 * sinh(0.5 * f.beta) / f.beta : 1.0;
-    // pulse bins: s_j within 9 sigma of tau, i.e. j in [(tau - 9 sigma)/Delta - 1/2, (tau + 9 sigma)/Delta - 1/2]
-    const double lo = (p.tau - kTailZ * p.sigma) / fc.delta - 0.5;
-    const double hi = (p.tau + kTailZ * p.sigma) / fc.delta - 0.5;
-    f.j_lo = lo < 0.0 ? 0 : (int)ceil(lo);
-    f.j_hi = hi >= (double)(p.N - 1) ? p.N - 1 : (int)floor(hi);
-    for (int b = threadIdx.x; b < 64; b += blockDim.x) t_lo[b] = exp(-f.beta * ((double)b + 0.5));
-    for (int a = threadIdx.x; a < nblk; a += blockDim.x) t_hi[a] = exp(-f.beta * (64.0 * (double)a));
-}
-
-// Factors of bin j (see batch_flux_setup): two FP64 products outside the
-// pulse, the FP64 erfc/exp evaluation inside it.
-__device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlux &f, const double *t_lo,
+// Factors of bin j: two FP64 products outside the pulse; inside it an FP64
+// erfc for G_j and two exponentials by exp_series.
+__device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const PixelConst &f, const double *t_lo,
                                                const double *t_hi, int j, float &w, float &u, float &lam_f) {
     const double g = t_hi[j >> 6] * t_lo[j & 63];                // exp(-B (j + 1/2) / N)
     if (j < f.j_lo || j > f.j_hi) {
@@ -375,8 +374,8 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
         const double s = ((double)j + 0.5) * f.delta;
         const double z = (s - p.tau) * f.inv_sigma;
         const double G = std_cdf(z) - f.Phi0;
-        const double lam = p.S * exp(-0.5 * z * z) * f.gnorm + f.bg;
-        const double wd = lam * exp(0.5 * f.Lambda - p.S * G) * g;
+        const double lam = p.S * exp_series(-0.5 * z * z) * f.gnorm + f.bg;
+        const double wd = lam * exp_series(0.5 * f.Lambda - p.S * G) * g;
         w = (float)wd;
         lam_f = (float)lam;
         u = lam_f / w;
@@ -391,7 +390,7 @@ __device__ __forceinline__ void batch_flux_bin(const PixelDev &p, const BatchFlu
 //   tail bins   w_j = w_j(point) 2 sinh(beta/2) / beta  (background only).
 // Each thread rewrites the bins it wrote in the flux loop.
 template <int NT>
-__device__ __forceinline__ void binint_pass(const PixelDev &p, const BatchFlux &f, const float *u, float *w,
+__device__ __forceinline__ void binint_pass(const PixelDev &p, const PixelConst &f, const float *u, float *w,
                                             float *v, int N) {
     for (int j = threadIdx.x; j < N; j += NT) {
         float x;
@@ -465,9 +464,9 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         const int ngroups = (N + span - 1) / span;
 
         // ---- K1: factors (FP64 inside), Lambda, eL
-        BatchFlux bf;
-        batch_flux_setup(p, bf, s_tlo, s_thi, (N + 63) >> 6);
-        const float eL = (float)exp(-bf.Lambda);
+        const PixelConst bf = a.pconst[item];
+        fill_geo_tables<NT>(bf, s_tlo, s_thi, (N + 63) >> 6);
+        const float eL = bf.eL;
         __syncthreads();
         const bool learned = a.warm != nullptr && a.warm_kind == 2;
         for (int j = tid; j < npad; j += NT) {
@@ -750,9 +749,9 @@ __global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs a) {
     for (int item = blockIdx.x; item < a.n; item += gridDim.x) {
         const PixelDev p = a.px[item];
         const int N = p.N, l = p.l;
-        BatchFlux bf;
-        batch_flux_setup(p, bf, s_tlo, s_thi, (N + 63) >> 6);
-        const float eL = (float)exp(-bf.Lambda);
+        const PixelConst bf = a.pconst[item];
+        fill_geo_tables<NT>(bf, s_tlo, s_thi, (N + 63) >> 6);
+        const float eL = bf.eL;
         __syncthreads();
         for (int j = tid; j < N; j += NT) {
             float wj, uj, lam;
@@ -867,6 +866,7 @@ cudaError_t launch_spectral(const SpectralArgs &a, int grid, cudaStream_t s) {
     const size_t smem = spectral_smem_bytes(a.npad_max);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if ((e = launch_pixel_const(a.px, a.n, a.pconst, s)) != cudaSuccess) return e;
     k<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1327,7 +1327,15 @@ static cudaError_t launch_batch_nt(const BatchArgs &a, int grid, size_t smem, cu
     return launch_batch_one<NT, 0, STRUCT>(a, grid, smem, s);
 }
 
+cudaError_t launch_pixel_const(const PixelDev *px, int n, PixelConst *out, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    pixel_const_kernel<<<(n + 127) / 128, 128, 0, s>>>(px, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = launch_pixel_const(a.px, a.n, a.pconst, s);
+    if (e != cudaSuccess) return e;
     if (a.structured) return launch_batch_nt<256, true>(a, grid, smem, s);
     if (threads == 512) return launch_batch_nt<512, false>(a, grid, smem, s);
     return launch_batch_nt<256, false>(a, grid, smem, s);

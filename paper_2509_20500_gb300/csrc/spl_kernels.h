@@ -42,6 +42,7 @@ struct BatchArgs {
     int min_iter;
     int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
     int flux_kind;           // spl_flux_kind_t: 0 point flux (Sec. 3.4), 1 bin-integrated
+    PixelConst *pconst;      // [n] per-pixel constants (work-list order), written by launch_batch
 };
 
 struct GemvArgs {
@@ -90,6 +91,7 @@ struct SpectralArgs {
     int pi_iters;            // power steps for pi (stops early at a 1e-7 step)
     int subspace_iters;      // orthogonal-iteration steps
     float *out;              // [n][2]: |lambda_2|, |arg lambda_2|
+    PixelConst *pconst;      // [n] per-pixel constants, written by launch_spectral
 };
 
 size_t spectral_smem_bytes(int npad);
@@ -100,6 +102,9 @@ size_t batch_smem_bytes(int npad, int level);
 int batch_state_level(int npad, bool structured);
 int batch_pad_len(int n);
 cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm);
+// The per-pixel constants of a work list (one thread per pixel); launch_batch
+// and launch_spectral run it before their kernels.
+cudaError_t launch_pixel_const(const PixelDev *px, int n, PixelConst *out, cudaStream_t s);
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal,

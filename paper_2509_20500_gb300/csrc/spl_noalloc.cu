@@ -40,9 +40,10 @@ constexpr int kNoAllocMaxBins = 3072;
 constexpr size_t kCounterBytes = 256;
 constexpr size_t kWorkBytes = sizeof(PixelDev) * kNoAllocMaxPixels;
 constexpr size_t kReportBytes = sizeof(ReportDev) * kNoAllocMaxPixels;
-constexpr size_t kScratchBytes = kCounterBytes + kWorkBytes + kReportBytes;
+constexpr size_t kConstBytes = sizeof(PixelConst) * kNoAllocMaxPixels;
+constexpr size_t kScratchBytes = kCounterBytes + kWorkBytes + kReportBytes + kConstBytes;
 
-// The scratch array (about 4 MB).  Host code must not use its name as an
+// The scratch array (about 13 MB).  Host code must not use its name as an
 // address: it is a host-side stand-in.  The device address comes from
 // cudaGetSymbolAddress, per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -129,6 +130,8 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     int *d_counter = reinterpret_cast<int *>(base);
     PixelDev *d_work = reinterpret_cast<PixelDev *>(base + kCounterBytes);
     ReportDev *d_reps = reinterpret_cast<ReportDev *>(base + kCounterBytes + kWorkBytes);
+    PixelConst *d_const = reinterpret_cast<PixelConst *>(base + kCounterBytes + kWorkBytes + kReportBytes);
+    static_assert((kCounterBytes + kWorkBytes + kReportBytes) % alignof(PixelConst) == 0, "constants alignment");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // Work list ordered by decreasing n_bins (counting sort, stable in the
@@ -186,6 +189,7 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     a.max_iter = max_iter;
     a.min_iter = 1;
     a.structured = 0;
+    a.pconst = d_const;
     if (launch_batch(a, threads, grid, smem, s) != cudaSuccess) return SPL_ECUDA;
 
     if (!h_reports) return SPL_OK;
