@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
 
         // ---- power iteration
         StopState st;
-        stop_init(st, tau);
+        stop_init(st, tau, a.warm != nullptr ? kWarmRhoFloor : 0.f);
         int status = ST_ENOCONV;
         // h_k = pi_{(k - l) mod N} * rho_k (J_l folded into the index) for the
         // first step; later steps get h from the statistics loop.
@@ -1280,7 +1280,7 @@ __global__ void __launch_bounds__(NT) init_iter_kernel(FinishArgs a, const float
     }
     if (tid == 0) {
         StopState st;
-        stop_init(st);
+        stop_init(st, 1.f, warm != nullptr ? kWarmRhoFloor : 0.f);
         a.state->st = st;
         a.state->done = 0;
         a.state->status = ST_ENOCONV;

@@ -8,11 +8,14 @@
 #include "../paper_2509_20500_gb300/csrc/spl_device.cuh"
 
 // Returns the step at which the rule ended (negative if it ended on an FP32
-// floor above the tolerance), 0 if it never did within K steps.
-extern "C" int stop_rule_replay(const double *d, int K, int M, float tol_err, int min_iter, float tau,
-                                float *err_out, float *rho_out, float *theta_out, int *reliable_out) {
+// floor above the tolerance), 0 if it never did within K steps.  tau is the
+// a priori bound on |lambda_2| (1: none); rho_floor as the kernels set it for
+// a warm start (0: a cold start).
+extern "C" int stop_rule_replay_warm(const double *d, int K, int M, float tol_err, int min_iter, float tau,
+                                     float rho_floor, float *err_out, float *rho_out, float *theta_out,
+                                     int *reliable_out) {
     spl::StopState s;
-    spl::stop_init(s, tau);
+    spl::stop_init(s, tau, rho_floor);
     int stop = 0;
     for (int k = 0; k < K; ++k) {
         const double *dk = d + (size_t)k * M;
@@ -37,3 +40,13 @@ extern "C" int stop_rule_replay(const double *d, int K, int M, float tol_err, in
     *reliable_out = s.reliable;
     return stop;
 }
+
+// A cold start (no warm-start floor).
+extern "C" int stop_rule_replay(const double *d, int K, int M, float tol_err, int min_iter, float tau,
+                                float *err_out, float *rho_out, float *theta_out, int *reliable_out) {
+    return stop_rule_replay_warm(d, K, M, tol_err, min_iter, tau, 0.f, err_out, rho_out, theta_out,
+                                 reliable_out);
+}
+
+// The warm-start floor the kernels use.
+extern "C" float stop_rule_warm_floor(void) { return spl::kWarmRhoFloor; }

@@ -34,17 +34,20 @@ def rule(tmp_path_factory):
                     "-gencode", "arch=compute_103a,code=sm_103a", "-o", out,
                     os.path.join(HERE, "stop_rule_host.cu")], check=True, capture_output=True)
     lib = ctypes.CDLL(out)
-    f = lib.stop_rule_replay
+    f = lib.stop_rule_replay_warm
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
-                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
-                  ctypes.POINTER(ctypes.c_int)]
+                  ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
+    lib.stop_rule_warm_floor.restype = ctypes.c_float
+    warm_floor = lib.stop_rule_warm_floor()
 
-    def replay(d, min_iter=1, tau=1.0):
+    def replay(d, min_iter=1, tau=1.0, warm=False):
         d = np.ascontiguousarray(d, dtype=np.float64)
         err, rho, th, rel = ctypes.c_float(), ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
-        k = f(d.ctypes.data, d.shape[0], d.shape[1], TOL_ERR, min_iter, float(tau), ctypes.byref(err),
-              ctypes.byref(rho), ctypes.byref(th), ctypes.byref(rel))
+        k = f(d.ctypes.data, d.shape[0], d.shape[1], TOL_ERR, min_iter, float(tau),
+              float(warm_floor if warm else 0.0), ctypes.byref(err), ctypes.byref(rho), ctypes.byref(th),
+              ctypes.byref(rel))
         return k, dict(err=err.value, rho=rho.value, theta=th.value, reliable=rel.value)
     return replay
 
@@ -156,6 +159,61 @@ def test_a_priori_bound_ends_a_fast_start_on_the_floor(rule, rho_fast, tau, nois
     assert true[k] < TOL
 
 
+@pytest.mark.parametrize("amp_slow", [1e-7, 2e-7, 4e-7, 8e-7, 1.6e-6])
+@pytest.mark.parametrize("seed", range(4))
+def test_warm_start_with_a_hidden_slow_mode(rule, amp_slow, seed):
+    """A warm start whose visible steps come from a fast mode (0.25) while a
+    slow mode (0.55, well below the a priori bound tau = 0.9) holds a small
+    error: the fits see only the fast mode.  With the warm-start floor every
+    stop is within the tolerance; without it (a cold start's rule) the same
+    sequences stop with a larger error."""
+    rng = np.random.default_rng(seed)
+    d, true = sequence(rng, 80, 2e-4, 0.25, 0.0, 5e-8, amp2=amp_slow, mu=0.55)
+    k, st = rule(d, tau=0.9, warm=True)
+    assert k > 0, st
+    assert true[k] < TOL, (k, true[k], st)
+    k_cold, _ = rule(d, tau=0.9)
+    assert abs(k_cold) <= k and true[abs(k_cold)] >= true[k]
+
+
+def test_warm_floor_on_a_real_chain(rule):
+    """The mechanism on a real chain (Eq. 6, a background-dominated pixel like
+    the array pixels where it showed): a start at pi plus a fast mode
+    (|lambda| ~ 0.21) and a small part of the slow pair (|lambda_2| ~ 0.55,
+    left eigenvectors from LAPACK).  A cold start's rule fits only the fast
+    mode; with the warm-start floor the stop comes later and closer to pi."""
+    import oracle
+    from paper_2509_20500_gb300 import workloads as W
+    p = W.as_dicts(W.pixel(200, 75.0, 38.0, 0.36, 0.03, 4.1))[0]
+    P = oracle.normalize_rows(oracle.build_reparam(p, oracle.shift_l(p)))
+    tau = 1.0 - P.min(axis=0).sum()
+    pi_star = oracle.power(P, tol=1e-15)[0]
+    ev, V = np.linalg.eig(P.T)
+    o = np.argsort(-np.abs(ev))
+    lam2 = abs(ev[o[1]])
+    slow = np.real(V[:, o[1]])
+    slow /= np.abs(slow).sum()
+    j = o[2:][np.argmin(np.abs(np.abs(ev[o[2:]]) - 0.2))]
+    fast = np.real(V[:, j])
+    fast /= np.abs(fast).sum()
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        pi = pi_star + 3e-4 * fast + (1e-6 if seed % 2 else -1e-6) * slow
+        ds, true = [], []
+        for _ in range(60):
+            y = pi @ P
+            y = y * (1.0 + 5e-8 * rng.standard_normal(200))
+            y /= y.sum()
+            ds.append(y - pi)
+            pi = y
+            true.append(np.abs(pi - pi_star).sum())
+        k_cold, st_cold = rule(np.array(ds), tau=tau)
+        k_warm, st_warm = rule(np.array(ds), tau=tau, warm=True)
+        assert st_cold["rho"] < 0.5 * lam2           # the fit misses the slow pair
+        assert k_warm >= k_cold and true[k_warm - 1] < true[k_cold - 1]
+        assert true[k_warm - 1] < 0.25 * TOL
+
+
 def test_min_iter_is_respected(rule):
     rng = np.random.default_rng(0)
     d, _ = sequence(rng, 50, 0.0, 0.5, 0.0, 1e-8)
@@ -231,7 +289,7 @@ def test_rigorous_stop_on_real_chains(rule, seed, noise):
                 ds.append(y - pi)
                 pi = y
                 true.append(np.abs(pi - pi_star).sum())
-            k, st = rule(np.array(ds), tau=min(1.0, tau + 1e-6))
+            k, st = rule(np.array(ds), tau=min(1.0, tau + 1e-6), warm=amp is not None)
             assert k != 0, (p, amp, st)
             if k > 0:
                 assert true[k - 1] < TOL, (p, amp, k, true[k - 1], tau, st)
