@@ -58,6 +58,13 @@ namespace spl {
 #define SPL_FFMA2 1
 #endif
 constexpr int kChain = SPL_KCHAIN;
+// Chunk length where the summed vector is spread out (the row pass, and
+// column passes whose iterate has sum_j pi_j^2 <= kFineIpr): there 256-row
+// chunks stay at the accuracy of 64-row ones (measured on 4096 array pixels:
+// FP32 fixed point within 2.1e-7 L1 below the threshold, up to 1.0e-6 above
+// it), at a quarter of the flushes.
+constexpr int kChainCoarse = 256;
+constexpr float kFineIpr = 0.01f;
 constexpr int kNch = SPL_NCH;
 
 // Compensated accumulation of a chunk sum x into (acc, comp) by Dekker's
@@ -105,7 +112,7 @@ __device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[
 // e % kNch), which are then added into the compensated outer accumulator:
 // relative rounding error per output about one FP32 unit roundoff instead of
 // ~15 for one sequential 2000-term chain.
-template <int C>
+template <int C, int KC = kChain>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
                                         float (&acc)[C], float (&comp)[C]) {
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
@@ -114,8 +121,8 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
     float2 mm[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) mm[c] = make_float2(m[c], m[c]);
-    for (int b0 = lo; b0 < hi; b0 += kChain) {
-        const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
+    for (int b0 = lo; b0 < hi; b0 += KC) {
+        const int q1 = (min(hi, b0 + KC) - b0) >> 2;
         float2 in01[C], in23[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) { in01[c] = make_float2(0.f, 0.f); in23[c] = make_float2(0.f, 0.f); }
@@ -134,8 +141,8 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
             fast_two_sum_acc(acc[c], comp[c], (in01[c].x + in01[c].y) + (in23[c].x + in23[c].y));
     }
 #else
-    for (int b0 = lo; b0 < hi; b0 += kChain) {
-        const int q1 = (min(hi, b0 + kChain) - b0) >> 2;
+    for (int b0 = lo; b0 < hi; b0 += KC) {
+        const int q1 = (min(hi, b0 + KC) - b0) >> 2;
         float in[kNch][C];
         chains_zero<C>(in);
 #pragma unroll 8
@@ -166,7 +173,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // for a chunk).  All bounds are multiples of 4; the span either starts at or
 // after b_lo, or lies fully below it; a span reaching past b_hi is cut at a
 // 32-entry block boundary (b_hi a multiple of 32 then).
-template <int C, bool kRowPass>
+template <int C, bool kRowPass, int KC = kChain>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
     float acc[C], comp[C];
@@ -178,7 +185,7 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         float m[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) m[c] = kRowPass ? mhi[c] : mlo[c];
-        tri_run<C>(v, b_lo, min(b_hi, base), m, acc, comp);
+        tri_run<C, KC>(v, b_lo, min(b_hi, base), m, acc, comp);
     }
     // the span itself (32 C entries, added as chunks of at most kChain)
     if (base >= b_lo && base < b_hi) {
@@ -219,7 +226,7 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
                     }
                 }
             }
-            if (((cb + 1) * 32) % kChain == 0 || cb == C - 1) {
+            if (((cb + 1) * 32) % KC == 0 || cb == C - 1) {
                 chains_flush<C>(in, acc, comp);
                 chains_zero<C>(in);
             }
@@ -230,7 +237,7 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         float m[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) m[c] = kRowPass ? mlo[c] : mhi[c];
-        tri_run<C>(v, max(b_lo, span_end), b_hi, m, acc, comp);
+        tri_run<C, KC>(v, max(b_lo, span_end), b_hi, m, acc, comp);
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) out[c] = acc[c] + comp[c];
@@ -501,7 +508,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                     mlo[c] = u;
                     mhi[c] = u * eL;
                 }
-                tri_pass<C, true>(sv, 0, nrow, base, lane, mlo, mhi, r);
+                tri_pass<C, true, kChainCoarse>(sv, 0, nrow, base, lane, mlo, mhi, r);
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const int k = base + 32 * c + lane;
@@ -574,11 +581,19 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                 lsum += x;
             }
         }
+        // sum_j pi_j^2 of the start picks the first column pass's chunk length
+        bool fine = 1.f / (float)N > kFineIpr;
         if (a.warm != nullptr) {
             const float tot = block_sum<NT>(lsum, red);
             const bool ok = tot > 0.f && isfinite(tot);
             const float inv = ok ? 1.f / tot : 0.f;
-            for (int j = tid; j < N; j += NT) spi[j] = ok ? spi[j] * inv : 1.f / (float)N;
+            float q2 = 0.f;
+            for (int j = tid; j < N; j += NT) {
+                const float x = ok ? spi[j] * inv : 1.f / (float)N;
+                spi[j] = x;
+                q2 = fmaf(x, x, q2);
+            }
+            fine = block_sum<NT>(q2, red) > kFineIpr;
         }
         for (int j = tid; j < N; j += NT) { gd1[j] = 0.f; gd2[j] = 0.f; }
         __syncthreads();
@@ -599,7 +614,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
             sv[k] = h;
         }
         __syncthreads();
-        // reduction scratch: [0, NW) step sums, [NW, 5 NW) step statistics,
+        // reduction scratch: [0, NW) step sums, [NW, 6 NW) step statistics,
         // [6 NW, 8 NW + 2) the structured step's scan; disjoint, so no buffer is
         // rewritten before every thread has read it
         float *redA = red;
@@ -628,7 +643,10 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                         mlo[c] = w;
                         mhi[c] = w * eL;
                     }
-                    tri_pass<C, false>(sv, 0, nrow, base, lane, mlo, mhi, y);
+                    if (fine)
+                        tri_pass<C, false, kChain>(sv, 0, nrow, base, lane, mlo, mhi, y);
+                    else
+                        tri_pass<C, false, kChainCoarse>(sv, 0, nrow, base, lane, mlo, mhi, y);
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
                         const int j = base + 32 * c + lane;
@@ -640,7 +658,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
             // one barrier: orders the y writes and ends every read of h
             const float s = block_sum_1bar<NT>(ysum, redA);
             const float inv = 1.f / s;
-            float stats[4] = {0.f, 0.f, 0.f, 0.f};
+            float stats[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             for (int j = tid; j < N; j += NT) {
                 const float pn = gy[j] * inv;
                 const float d = pn - spi[j];
@@ -649,6 +667,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                 stats[1] = fmaf(d, d, stats[1]);
                 stats[2] = fmaf(d, e1, stats[2]);
                 stats[3] = fmaf(d, e2, stats[3]);
+                stats[4] = fmaf(pn, pn, stats[4]);
                 gd2[j] = e1;
                 gd1[j] = d;
                 spi[j] = pn;
@@ -658,7 +677,8 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                 sv[k] = pn * srho[k];
             }
             // one barrier: orders pi, d and h before the next step
-            block_sum_k_1bar<NT, 4>(stats, redS);
+            block_sum_k_1bar<NT, 5>(stats, redS);
+            fine = stats[4] > kFineIpr;
             const int su = stop_update(st, stats[0], stats[1], stats[2], stats[3], a.tol_err, a.min_iter);
             if (su != STOP_CONTINUE) {
                 status = su == STOP_CONVERGED ? ST_OK : ST_ENOCONV;
