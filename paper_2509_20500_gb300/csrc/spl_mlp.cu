@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_bf16_kernel(const __grid
     __shared__ uint32_t tmem_base;
     __shared__ float s_bias[BN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // N tiles vary fastest, so the CTAs that share an A tile (one 128-row
+    // slice of the activations) run together and read it once from HBM
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KB = g.K / BK;
     if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
         for (int c = threadIdx.x; c < BN; c += kGemmThreads) s_bias[c] = (n0 + c < g.N) ? g.bias[n0 + c] : 0.f;
@@ -406,7 +408,7 @@ cudaError_t launch_gemm_mode(const CUtensorMap &ta, const CUtensorMap &tb, const
     auto k = gemm_bf16_kernel<MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     if (e != cudaSuccess) return e;
-    dim3 grid(g.M / BM, (g.N + BN - 1) / BN);
+    dim3 grid((g.N + BN - 1) / BN, g.M / BM);
     k<<<grid, kGemmThreads, kGemmSmem, s>>>(ta, tb, g);
     return cudaGetLastError();
 }
