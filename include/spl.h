@@ -165,6 +165,13 @@ typedef struct {
     int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
     int32_t pass_kind;        /* spl_pass_kind_t */
     int32_t flux_kind;        /* spl_flux_kind_t */
+    int32_t tune;             /* launch configuration: 0 (default) 256-thread blocks with the state level and
+                                 blocks per SM measured on the first batch of at least 1024 pixels of a kind
+                                 (padded n_bins, pass kind, SM count) and cached, also in the file
+                                 SPL_TUNE_CACHE names if set; these choices give the same pmfs bit for bit.
+                                 1 fixed heuristic; 2 explicit threads and state_level.  threads = 512 changes
+                                 the order of the block reductions (results within rounding, not bitwise). */
+    int32_t state_level;      /* tune == 2: per-pixel vectors in shared memory (2 all, 1 three, 0 one) */
 } spl_batch_opts_t;
 
 /* spl_batch_stationary with options (opts may be NULL for the defaults). */
@@ -208,6 +215,13 @@ SPL_API spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t n, 
  */
 SPL_API spl_status_t spl_mc_histograms(const spl_pixel_t *h_pixels, int32_t n, int32_t runs, int64_t cycles,
                                        uint64_t seed, uint32_t *d_hist, void *stream);
+
+/* The measured launch configuration cached for batches whose largest pixel
+ * has n_bins_max bins and pass kind pass_kind on the current device:
+ * SPL_OK with *threads, *state_level and *blocks_per_sm, or SPL_ENOCONV if
+ * none is cached yet. */
+SPL_API spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_kind, int32_t *threads,
+                                           int32_t *state_level, int32_t *blocks_per_sm);
 
 /* Device time in ms of the batch kernel of the last spl_batch_stationary_ex
  * call on the current device that set time_kernel (events recorded on that

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -140,7 +143,16 @@ struct spl_chain {
     int gemv_grid = 0, tiles_per_slab = 0, tiles_per_cta = 0, total_tiles = 0;
     // fused split
     int chunks = 0, chunk = 0, ld_part = 0;
+    // kGraphSteps power steps captured once as a CUDA graph, replayed per chunk
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t steps_exec = nullptr;
+    bool graph_failed = false;
 };
+
+// Steps per replay of the captured chunk.  Every kernel returns at once when
+// the device state says the iteration is done, so steps issued past the stop
+// cost only their launch.
+constexpr int kGraphSteps = 8;
 
 static void chain_release(spl_chain *c) {
     if (!c) return;
@@ -149,6 +161,8 @@ static void chain_release(spl_chain *c) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->steps_exec) cudaGraphExecDestroy(c->steps_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -284,8 +298,7 @@ static FinishArgs finish_args(spl_chain *c) {
 
 // One power step: the dense pass (GEMV over P, or the regenerated split
 // column pass) followed by the finish kernel.
-static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa) {
-    cudaStream_t s = c->stream;
+static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa, cudaStream_t s) {
     cudaError_t e;
     if (c->mode == SPL_MATERIALIZED) {
         GemvArgs g{};
@@ -318,6 +331,31 @@ static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa) {
     return SPL_OK;
 }
 
+// Captures kGraphSteps power steps of this chain once (on a private stream,
+// so the caller's stream may be the legacy default stream) and keeps the
+// executable graph; returns false if capture is unavailable, in which case the
+// steps are launched one by one.
+static bool chain_graph(spl_chain *c, const FinishArgs &fa) {
+    if (c->steps_exec) return true;
+    if (c->graph_failed) return false;
+    bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    if (ok) ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        for (int i = 0; i < kGraphSteps && ok; ++i) ok = chain_step(c, fa, c->cap_stream) == SPL_OK;
+        const bool ended = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess;
+        ok = ok && ended && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&c->steps_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        c->steps_exec = nullptr;
+        c->graph_failed = true;
+        (void)cudaGetLastError();   // capture problems are not errors of the call
+    }
+    return ok;
+}
+
 extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_iter, const float *d_warm,
                                        float *d_pi, spl_report_t *rep) {
     if (!c || !d_pi || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
@@ -333,13 +371,18 @@ extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_i
     SPL_CU(launch_init_iter(fa, d_warm, s));
     // Steps are issued in chunks; every kernel exits at once when the device
     // state says done, so over-issuing within a chunk costs only launches.
+    const bool graph = chain_graph(c, fa);
     int issued = 0;
-    const int chunk = 4;
+    const int chunk = graph ? kGraphSteps : 4;
     for (;;) {
-        const int n = std::min(chunk, max_iter - issued);
-        for (int i = 0; i < n; ++i) {
-            spl_status_t st = chain_step(c, fa);
-            if (st != SPL_OK) return st;
+        const int n = graph ? chunk : std::min(chunk, max_iter - issued);
+        if (graph) {
+            SPL_CU(cudaGraphLaunch(c->steps_exec, s));
+        } else {
+            for (int i = 0; i < n; ++i) {
+                spl_status_t st = chain_step(c, fa, s);
+                if (st != SPL_OK) return st;
+            }
         }
         issued += n;
         SPL_CU(cudaMemcpyAsync(c->h_state, c->state, sizeof(ChainState), cudaMemcpyDeviceToHost, s));
@@ -576,33 +619,146 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
     return SPL_OK;
 }
 
+// ---------------------------------------------------------------- batch launch configuration
+//
+// A configuration is the block size (256 or 512 threads), the state level
+// (how many per-pixel vectors live in shared memory) and the blocks per SM.
+// The state level and the blocks per SM only move vectors between shared and
+// global memory and change how many pixels run at once, never the order of a
+// sum, so they give the same pmfs bit for bit; the block size changes the
+// block reductions' order (rounding) and is not measured, only taken when
+// the caller asks for it.  The rest is measured: on the first large batch of
+// a kind (padded N, pass kind, SM count) every feasible 256-thread
+// configuration runs a sample of the work list (after an untimed launch that
+// absorbs module loading), the fastest per pixel is kept in a cache, and
+// SPL_TUNE_CACHE (a file path, optional) keeps the cache across processes.
+
+struct LaunchCfg {
+    int threads = 256, level = 2, bps = 0;   // bps: blocks per SM (at most the occupancy limit)
+    size_t smem = 0;
+};
+
+spl_status_t batch_cfg(int threads, int level, int npad, bool structured, LaunchCfg *cfg) {
+    if (threads != 256 && threads != 512) return SPL_EINVAL;
+    if (structured && threads != 256) return SPL_EINVAL;
+    if (level < 0 || level > 2) return SPL_EINVAL;
+    cfg->threads = threads;
+    cfg->level = level;
+    cfg->smem = batch_smem_bytes(npad, level);
+    if (cfg->smem > 220 * 1024) return SPL_EINVAL;
+    int bps = 0;
+    SPL_CU(batch_occupancy(threads, level, structured, cfg->smem, &bps));
+    if (bps < 1) return SPL_EINVAL;
+    cfg->bps = bps;
+    return SPL_OK;
+}
+
+using TuneKey = std::array<int, 3>;      // padded N, structured, SMs
+using TuneVal = std::array<int, 3>;      // threads, state level, blocks per SM
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+bool g_tune_loaded = false;
+constexpr int32_t kTuneMinPixels = 1024;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("SPL_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE *f = std::fopen(path, "r")) {
+        int v[6];
+        while (std::fscanf(f, "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6)
+            g_tune[TuneKey{v[0], v[1], v[2]}] = TuneVal{v[3], v[4], v[5]};
+        std::fclose(f);
+    }
+}
+
+void tune_store_locked(const TuneKey &k, const TuneVal &v) {
+    g_tune[k] = v;
+    const char *path = std::getenv("SPL_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "%d %d %d %d %d %d\n", k[0], k[1], k[2], v[0], v[1], v[2]);
+        std::fclose(f);
+    }
+}
+
+bool tune_lookup(const TuneKey &k, TuneVal *v) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+// One launch of the batch kernel over the first n items of the uploaded work
+// list with configuration cfg (a holds everything else).
+spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, int32_t n, int npad,
+                        cudaStream_t s) {
+    int grid = cfg.bps * num_sms_current();
+    if (grid > n) grid = n;
+    const size_t per_block = cfg.level == 2 ? 0 : (size_t)(cfg.level == 1 ? 5 : 7) * npad;
+    cudaError_t e;
+    if (per_block && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * per_block)) != cudaSuccess)
+        return status_of_alloc(e, "scratch");
+    SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
+    a.n = n;
+    a.scratch = ws.scratch;
+    a.state_level = cfg.level;
+    SPL_CU(launch_batch(a, cfg.threads, grid, cfg.smem, s));
+    return SPL_OK;
+}
+
+// Times every feasible configuration on a sample of the work list and keeps
+// the fastest (per pixel).
+spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int npad, bool structured,
+                        cudaStream_t s, LaunchCfg *best) {
+    const int sms = num_sms_current();
+    const int32_t sample = std::min<int32_t>(n, 12 * sms);
+    if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
+    if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
+    float best_ms = INFINITY;
+    for (int level = 2; level >= 0; --level) {
+        LaunchCfg top;
+        if (batch_cfg(256, level, npad, structured, &top) != SPL_OK) continue;
+        for (int bps = top.bps; bps >= std::max(1, top.bps - 1); --bps) {
+            LaunchCfg cfg = top;
+            cfg.bps = bps;
+            // untimed: loads the kernel's module and settles the clocks
+            spl_status_t st = launch_cfg(ws, a, cfg, std::min<int32_t>(sample, cfg.bps * sms), npad, s);
+            if (st != SPL_OK) return st;
+            SPL_CU(cudaEventRecord(ws.ev0, s));
+            if ((st = launch_cfg(ws, a, cfg, sample, npad, s)) != SPL_OK) return st;
+            SPL_CU(cudaEventRecord(ws.ev1, s));
+            SPL_CU(cudaEventSynchronize(ws.ev1));
+            float ms = 0.f;
+            SPL_CU(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = cfg;
+            }
+        }
+    }
+    return std::isfinite(best_ms) ? SPL_OK : SPL_EINVAL;
+}
+
 // Launches the persistent batch kernel; out/warm are packed by caller order.
+// tune: 0 measured configuration (cached), 1 the fixed heuristic, 2 the
+// caller's threads and state level.
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
-                       cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0) {
-    const int threads = threads_req > 0 ? threads_req : batch_threads_for(nmax);
-    if (threads != 256 && threads != 512) return SPL_EINVAL;
+                       cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0,
+                       int tune = 0, int level_req = -1) {
     const int npad = batch_pad_len(nmax);
-    // Per-pixel vectors go to shared memory as far as three blocks per SM allow.
-    const int level = batch_state_level(npad, structured != 0);
-    const size_t smem = batch_smem_bytes(npad, level);
-    if (smem > 220 * 1024) return SPL_EINVAL;
-    int bps = 0;
-    SPL_CU(batch_occupancy(threads, level, structured != 0, smem, &bps));
-    if (bps < 1) return SPL_EINVAL;
-    int grid = bps * num_sms_current();
-    if (grid > n) grid = n;
+    const bool st_kind = structured != 0;
     cudaError_t e;
     if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
     if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
     if ((e = grow(&ws.counter, &ws.counter_cap, 1)) != cudaSuccess) return status_of_alloc(e, "counter");
     if ((e = grow(&ws.pconst, &ws.pconst_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "constants");
-    const size_t per_block = level == 2 ? 0 : (size_t)(level == 1 ? 5 : 7) * npad;
-    if (per_block && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * per_block)) != cudaSuccess)
-        return status_of_alloc(e, "scratch");
     SPL_CU(cudaMemcpyAsync(ws.px, ws.h_px, sizeof(PixelDev) * n, cudaMemcpyHostToDevice, s));
-    SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
     BatchArgs a{};
     a.px = ws.px;
     a.n = n;
@@ -613,21 +769,49 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.out = d_out;
     a.offsets = d_offsets;
     a.reports = ws.reps;
-    a.scratch = ws.scratch;
     a.npad_max = npad;
-    a.state_level = level;
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);
     a.structured = structured;
     a.flux_kind = flux_kind;
     a.pconst = ws.pconst;
+
+    LaunchCfg cfg;
+    spl_status_t st;
+    if (tune == 2 || threads_req > 0) {
+        const int level = level_req >= 0 ? level_req : batch_state_level(npad, st_kind);
+        if ((st = batch_cfg(threads_req > 0 ? threads_req : 256, level, npad, st_kind, &cfg)) != SPL_OK)
+            return st;
+    } else {
+        // heuristic: 256 threads, the largest state level that keeps three
+        // blocks' vectors in shared memory
+        if ((st = batch_cfg(batch_threads_for(nmax), batch_state_level(npad, st_kind), npad, st_kind, &cfg)) !=
+            SPL_OK)
+            return st;
+        if (tune == 0) {
+            const TuneKey key{npad, structured, num_sms_current()};
+            TuneVal v;
+            LaunchCfg c2;
+            if (tune_lookup(key, &v) && v[0] == 256 && batch_cfg(v[0], v[1], npad, st_kind, &c2) == SPL_OK &&
+                v[2] >= 1 && v[2] <= c2.bps) {
+                c2.bps = v[2];
+                cfg = c2;
+            } else if (n >= kTuneMinPixels) {
+                if ((st = tune_batch(ws, a, n, npad, st_kind, s, &c2)) != SPL_OK) return st;
+                cfg = c2;
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                tune_load_locked();
+                tune_store_locked(key, TuneVal{cfg.threads, cfg.level, cfg.bps});
+            }
+        }
+    }
     if (time_kernel) {
         if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
         SPL_CU(cudaEventRecord(ws.ev0, s));
     }
-    SPL_CU(launch_batch(a, threads, grid, smem, s));
+    if ((st = launch_cfg(ws, a, cfg, n, npad, s)) != SPL_OK) return st;
     if (time_kernel) {
         SPL_CU(cudaEventRecord(ws.ev1, s));
         ws.timed = true;
@@ -684,8 +868,11 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
     const int flux_kind = opts ? opts->flux_kind : 0;
     if (flux_kind != SPL_FLUX_POINT && flux_kind != SPL_FLUX_BININT) return SPL_EINVAL;
+    const int tune = opts ? opts->tune : 0;
+    const int level = opts ? opts->state_level : -1;
+    if (tune < 0 || tune > 2 || (tune == 2 && (level < 0 || level > 2))) return SPL_EINVAL;
     st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed,
-                   structured, flux_kind);
+                   structured, flux_kind, tune, tune == 2 ? level : -1);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the
@@ -757,6 +944,19 @@ extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t 
     const int grid = std::min(n, 2 * num_sms_current());
     SPL_CU(launch_spectral(a, grid, s));
     SPL_CU(cudaStreamSynchronize(s));   // the pinned work list is reused by the next call
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_kind, int32_t *threads,
+                                              int32_t *state_level, int32_t *blocks_per_sm) {
+    if (n_bins_max < 2 || !threads || !state_level || !blocks_per_sm) return SPL_EINVAL;
+    if (pass_kind != SPL_PASS_DENSE && pass_kind != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    const TuneKey key{batch_pad_len(n_bins_max), pass_kind, num_sms_current()};
+    TuneVal v;
+    if (!tune_lookup(key, &v)) return SPL_ENOCONV;
+    *threads = v[0];
+    *state_level = v[1];
+    *blocks_per_sm = v[2];
     return SPL_OK;
 }
 

@@ -38,7 +38,7 @@ class spl_report_t(ctypes.Structure):
 class spl_batch_opts_t(ctypes.Structure):
     _fields_ = [("warm_kind", ctypes.c_int32), ("warm_ld", ctypes.c_int32), ("min_iter", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32), ("pass_kind", ctypes.c_int32),
-                ("flux_kind", ctypes.c_int32)]
+                ("flux_kind", ctypes.c_int32), ("tune", ctypes.c_int32), ("state_level", ctypes.c_int32)]
 
 
 SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
@@ -56,7 +56,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
-            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward"]
+            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
 
 _lib = None
 _lock = threading.Lock()
@@ -126,6 +126,9 @@ def lib():
         L.spl_mlp_forward.restype = ctypes.c_int
         L.spl_mlp_time_forward.argtypes = [vp, P, i32, i32, fp]
         L.spl_mlp_time_forward.restype = ctypes.c_int
+        L.spl_batch_tune_lookup.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]
+        L.spl_batch_tune_lookup.restype = ctypes.c_int
         L.spl_mlp_loss_grad.argtypes = [vp, P, i32, vp, fp, vp]
         L.spl_mlp_loss_grad.restype = ctypes.c_int
         L.spl_mlp_train_step.argtypes = [vp, P, i32, vp, ctypes.c_float, ctypes.c_float, fp]
@@ -267,7 +270,8 @@ class Chain:
 def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
                      warm_kind: int = SPL_WARM_WEIGHTS, warm_ld: int = 0, min_iter: int = 1, threads: int = 0,
                      reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None,
-                     pass_kind: int = SPL_PASS_DENSE, flux_kind: int = SPL_FLUX_POINT):
+                     pass_kind: int = SPL_PASS_DENSE, flux_kind: int = SPL_FLUX_POINT, tune: int = 0,
+                     state_level: int = -1):
     """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
     import torch
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
@@ -280,7 +284,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
     arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
     opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)),
-                            int(pass_kind), int(flux_kind))
+                            int(pass_kind), int(flux_kind), int(tune), int(state_level))
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
@@ -307,6 +311,19 @@ def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 
                                             _dptr(offsets), reps, _stream_ptr(stream))
     _check(st, "spl_batch_stationary_noalloc", (SPL_OK, SPL_ENOCONV))
     return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+
+def batch_tune_lookup(n_bins_max: int, pass_kind: int = SPL_PASS_DENSE):
+    """The cached measured launch configuration (threads, state level, blocks
+    per SM) for batches of this size and pass kind on the current device, or
+    None."""
+    t, lv, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    st = lib().spl_batch_tune_lookup(int(n_bins_max), int(pass_kind), ctypes.byref(t), ctypes.byref(lv),
+                                     ctypes.byref(b))
+    if st == SPL_ENOCONV:
+        return None
+    _check(st, "spl_batch_tune_lookup")
+    return int(t.value), int(lv.value), int(b.value)
 
 
 def mc_histograms(px: np.ndarray, runs: int, cycles: int, seed: int, out=None, stream=None):
@@ -433,7 +450,7 @@ class MLP:
             out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
-        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind), int(flux_kind))
+        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind), int(flux_kind), 0, -1)
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
                                                 _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))

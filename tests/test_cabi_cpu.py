@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(S):
 def test_struct_layouts(S):
     assert ctypes.sizeof(S.spl_pixel_t) == 56 == W.PIXEL_DTYPE.itemsize
     assert ctypes.sizeof(S.spl_report_t) == 24 == S.REPORT_DTYPE.itemsize
-    assert ctypes.sizeof(S.spl_batch_opts_t) == 28
+    assert ctypes.sizeof(S.spl_batch_opts_t) == 36
 
 
 def test_strerror_and_version(S):

@@ -462,3 +462,44 @@ def test_spectral_statements_of_sec4_on_gpu(spl):
         assert np.all(np.diff(res[t_d][:, :, 0], axis=1) > 0)
     assert np.all(np.diff(res[75.0][:, 1:, 1], axis=1) > 0)
     assert np.all(res[95.0][3:, :, 1] < 0.2)
+
+
+@pytest.mark.parametrize("pass_kind", ["dense", "structured"])
+def test_every_launch_configuration_gives_the_same_pmfs(spl, pass_kind):
+    """The state level only moves vectors between shared and global memory:
+    every level the autotuner may pick gives the same pmfs bit for bit
+    (ragged N up to 9000, which reaches every level).  512-thread blocks sum
+    their reductions in another order: within the parity tolerance of the
+    256-thread result."""
+    pk = spl.SPL_PASS_DENSE if pass_kind == "dense" else spl.SPL_PASS_STRUCTURED
+    px = np.concatenate([W.random_small(6, seed=71, n_min=20, n_max=300), W.array_pixels(3, seed=72),
+                         W.pixel(9000, 40.0, 30.0, 0.3, 0.5, 0.5), W.pixel(4100, 130.0, 60.0, 0.8, 2.0, 1.0)])
+    ref, off, _ = spl.batch_stationary(px, pass_kind=pk, tune=1)
+    ref = ref.cpu().numpy()
+    seen = 0
+    for level in (2, 1, 0):
+        try:
+            o, _, _ = spl.batch_stationary(px, pass_kind=pk, tune=2, threads=256, state_level=level)
+        except spl.SplError as e:
+            assert e.status == spl.SPL_EINVAL     # infeasible here (shared memory)
+            continue
+        np.testing.assert_array_equal(o.cpu().numpy(), ref)
+        seen += 1
+    assert seen >= 2
+    if pass_kind == "dense":
+        o, _, _ = spl.batch_stationary(px, pass_kind=pk, tune=2, threads=512, state_level=0)
+        o = o.cpu().numpy().astype(np.float64)
+        for k in range(len(px)):
+            assert _l1(o[off[k]:off[k + 1]], ref[off[k]:off[k + 1]].astype(np.float64)) < 1e-6
+
+
+def test_autotuned_batch_is_cached_and_unchanged(spl):
+    """A batch of at least 1024 pixels measures the launch configurations
+    once and caches the fastest; the result equals the heuristic launch's."""
+    px = W.array_pixels(1536, seed=73, n_bins=700)
+    a, off, _ = spl.batch_stationary(px, tol=1e-6)
+    cfg = spl.batch_tune_lookup(700)
+    assert cfg is not None and cfg[0] == 256 and cfg[1] in (0, 1, 2) and cfg[2] >= 1
+    b, _, _ = spl.batch_stationary(px, tol=1e-6, tune=1)
+    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert spl.batch_tune_lookup(700) == cfg
