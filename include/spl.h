@@ -326,9 +326,19 @@ SPL_API spl_status_t spl_matrix(spl_chain_t *c, float *d_P);
 
 /* Measurement: device time of one dense power-step pass of a chain (the
  * TMA GEMV over the stored P, or the split regenerating column pass),
- * averaged over `reps` back-to-back passes after one warm-up pass; CUDA
- * events on the chain's stream.  Leaves the chain's iterate reset. */
+ * averaged over `reps` passes captured in one CUDA graph (so no host launch
+ * overhead) and replayed after one untimed replay; CUDA events on the
+ * chain's stream.  Leaves the chain's iterate reset. */
 SPL_API spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass);
+
+/* Measurement: device time of one whole power step of a chain (the dense
+ * pass, the reduction of its partials, normalisation, step statistics, stop
+ * rule and next broadcast vector) with the stop rule held open: materialised
+ * chains as reps steps replayed from a captured graph, fused chains as one
+ * persistent launch of reps steps (which makes one more pass for its lagged
+ * stop decision), each after an untimed run.  Leaves the chain's iterate
+ * reset. */
+SPL_API spl_status_t spl_chain_time_step(spl_chain_t *c, int32_t reps, float *ms_per_step);
 
 /* Measurement: device time of the materialised build (the write of P and its
  * row sums, Eq. 6 with the roll in the row address), averaged over `reps`

@@ -137,12 +137,20 @@ struct spl_chain {
     ChainState *state = nullptr;
     ChainState *h_state = nullptr;   // pinned readback
     int *err_flag = nullptr;
+    float *blk = nullptr;            // finish stages' per-CTA partials
+    int *ticket = nullptr;           // finish stages' arrival counters
     // materialised
     float *P = nullptr;
     CUtensorMap tmap{};
     int gemv_grid = 0, tiles_per_slab = 0, tiles_per_cta = 0, total_tiles = 0;
-    // fused split
+    // fused split (row pass at build, standalone pass timing)
     int chunks = 0, chunk = 0, ld_part = 0;
+    // fused persistent iteration: grid, tiles, row chunks and its buffers
+    int run_grid = 0, run_T = 0, run_RB = 0, run_segs = 0, run_chunk = 0;
+    float *run_y = nullptr, *run_vb = nullptr, *run_pi = nullptr, *run_tsum = nullptr, *run_part = nullptr,
+          *run_blk = nullptr;
+    int *run_ticket = nullptr;
+    unsigned *run_bar = nullptr;
     // kGraphSteps power steps captured once as a CUDA graph, replayed per chunk
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t steps_exec = nullptr;
@@ -157,7 +165,9 @@ constexpr int kGraphSteps = 8;
 static void chain_release(spl_chain *c) {
     if (!c) return;
     void *bufs[] = {c->w, c->u, c->lam, c->F, c->scal, c->rowsum, c->rho, c->pi, c->y,
-                    c->d1, c->d2, c->v, c->part, c->state, c->err_flag, c->P};
+                    c->d1, c->d2, c->v, c->part, c->state, c->err_flag, c->P, c->blk, c->ticket,
+                    c->run_y, c->run_vb, c->run_pi, c->run_tsum, c->run_part, c->run_blk, c->run_ticket,
+                    c->run_bar};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_state) cudaFreeHost(c->h_state);
@@ -182,6 +192,9 @@ static spl_status_t chain_alloc(spl_chain *c) {
     SPL_CU(dalloc(&c->v, vl));
     SPL_CU(dalloc(&c->state, 1));
     SPL_CU(dalloc(&c->err_flag, 1));
+    SPL_CU(dalloc(&c->blk, finish_blk_floats(vl)));
+    SPL_CU(dalloc(&c->ticket, 2));
+    SPL_CU(cudaMemset(c->ticket, 0, 2 * sizeof(int)));
     SPL_CU(cudaMallocHost(reinterpret_cast<void **>(&c->h_state), sizeof(ChainState)));
     return SPL_OK;
 }
@@ -198,6 +211,73 @@ static void plan_split(spl_chain *c) {
     c->chunk = blk_per_chunk * 128;
     c->chunks = (c->vlen + c->chunk - 1) / c->chunk;
     c->ld_part = c->vlen;
+}
+
+// Plan of the persistent fused iteration: as many CTAs as stay resident (at
+// most one per work unit), the work units (128-column tile x 32-row block)
+// split evenly over them, and the partial slots one CTA needs.
+static spl_status_t plan_run(spl_chain *c) {
+    const int sms = num_sms_current();
+    const int maxc = chain_run_max_chunk();
+    const int bps = std::min(2, chain_run_blocks_per_sm(maxc));
+    if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "chain run occupancy");
+    const int T = (c->N + chain_run_tile_cols() - 1) / chain_run_tile_cols();
+    const int RB = c->vlen / 32;
+    const long long U = (long long)T * RB;
+    const int G = (int)std::min<long long>(std::min(bps * sms, chain_run_max_grid()), U);
+    int segs = 1;
+    long long umax = 0;
+    for (int b = 0; b < G; ++b) {
+        const long long u0 = (long long)b * U / G, u1 = (long long)(b + 1) * U / G;
+        segs = std::max(segs, (int)((u1 - 1) / RB - u0 / RB) + 1);
+        umax = std::max(umax, u1 - u0);
+    }
+    c->run_T = T;
+    c->run_RB = RB;
+    c->run_segs = segs;
+    c->run_chunk = (int)std::min<long long>(maxc, umax * 32);
+    c->run_grid = G;
+    SPL_CU(dalloc(&c->run_y, 2 * (size_t)c->vlen));
+    SPL_CU(dalloc(&c->run_vb, 2 * (size_t)c->vlen));
+    SPL_CU(cudaMemset(c->run_vb, 0, 2 * sizeof(float) * c->vlen));
+    SPL_CU(dalloc(&c->run_pi, (size_t)c->N));
+    SPL_CU(dalloc(&c->run_tsum, 2 * (size_t)T));
+    SPL_CU(dalloc(&c->run_part, (size_t)G * segs * chain_run_tile_cols()));
+    SPL_CU(dalloc(&c->run_blk, 2 * (size_t)G * 4));
+    SPL_CU(dalloc(&c->run_ticket, (size_t)T));
+    SPL_CU(dalloc(&c->run_bar, (size_t)chain_run_bar_words()));
+    SPL_CU(cudaMemset(c->run_ticket, 0, sizeof(int) * T));
+    SPL_CU(cudaMemset(c->run_bar, 0, sizeof(unsigned) * chain_run_bar_words()));
+    return SPL_OK;
+}
+
+static ChainRunArgs run_args(spl_chain *c) {
+    ChainRunArgs a{};
+    a.N = c->N;
+    a.vlen = c->vlen;
+    a.l = c->p.l;
+    a.T = c->run_T;
+    a.RB = c->run_RB;
+    a.segs = c->run_segs;
+    a.chunk = c->run_chunk;
+    a.w = c->w;
+    a.scal = c->scal;
+    a.rho = c->rho;
+    a.v0 = c->v;
+    a.pi = c->pi;
+    a.pi_alt = c->run_pi;
+    a.d1 = c->d1;
+    a.d2 = c->d2;
+    a.y = c->run_y;
+    a.vb = c->run_vb;
+    a.tsum = c->run_tsum;
+    a.part = c->run_part;
+    a.blk = c->run_blk;
+    a.tile_ticket = c->run_ticket;
+    a.bar = c->run_bar;
+    a.state = c->state;
+    a.err_flag = c->err_flag;
+    return a;
 }
 
 extern "C" spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *stream, spl_chain_t **out) {
@@ -269,6 +349,8 @@ extern "C" spl_status_t spl_build(const spl_pixel_t *p, spl_mode_t mode, void *s
         if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "row pass"); }
         e = launch_finish_rows(d.N, c->chunks, c->ld_part, c->part, c->u, c->rho, c->rowsum, d.l, s);
         if (e != cudaSuccess) { chain_release(c); return cuda_fail(e, "finish rows"); }
+        st = plan_run(c);
+        if (st != SPL_OK) { chain_release(c); return st; }
     }
     *out = c;
     return SPL_OK;
@@ -293,12 +375,14 @@ static FinishArgs finish_args(spl_chain *c) {
     a.rho = c->rho;
     a.v = c->v;
     a.state = c->state;
+    a.blk = c->blk;
+    a.ticket = c->ticket;
     return a;
 }
 
-// One power step: the dense pass (GEMV over P, or the regenerated split
-// column pass) followed by the finish kernel.
-static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa, cudaStream_t s) {
+// The dense pass of one power step: GEMV over P, or the regenerated split
+// column pass; partial column sums into c->part.
+static spl_status_t chain_pass(spl_chain *c, cudaStream_t s) {
     cudaError_t e;
     if (c->mode == SPL_MATERIALIZED) {
         GemvArgs g{};
@@ -326,8 +410,41 @@ static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa, cudaStream_t 
         e = launch_tri_split(ta, false, c->chunks, s);
         if (e != cudaSuccess) return cuda_fail(e, "column pass");
     }
-    e = launch_finish_step(fa, s);
+    return SPL_OK;
+}
+
+// One power step: the dense pass followed by the two finish kernels.
+static spl_status_t chain_step(spl_chain *c, const FinishArgs &fa, cudaStream_t s) {
+    spl_status_t st = chain_pass(c, s);
+    if (st != SPL_OK) return st;
+    cudaError_t e = launch_finish_step(fa, s);
     if (e != cudaSuccess) return cuda_fail(e, "finish step");
+    return SPL_OK;
+}
+
+// Captures reps dense passes (whole_step false) or reps whole power steps on
+// the chain's capture stream into an executable graph.
+static spl_status_t capture_reps(spl_chain *c, const FinishArgs &fa, int reps, bool whole_step,
+                                 cudaGraphExec_t *exec) {
+    *exec = nullptr;
+    if (!c->cap_stream) SPL_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    SPL_CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    spl_status_t st = SPL_OK;
+    for (int i = 0; i < reps && st == SPL_OK; ++i)
+        st = whole_step ? chain_step(c, fa, c->cap_stream) : chain_pass(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != SPL_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return st != SPL_OK ? st : cuda_fail(e != cudaSuccess ? e : cudaErrorStreamCaptureInvalidated, "capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        *exec = nullptr;
+        return cuda_fail(ei, "graph instantiate");
+    }
     return SPL_OK;
 }
 
@@ -356,6 +473,8 @@ static bool chain_graph(spl_chain *c, const FinishArgs &fa) {
     return ok;
 }
 
+static spl_status_t chain_report(spl_chain *c, cudaStream_t s, float *d_pi, spl_report_t *rep);
+
 extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_iter, const float *d_warm,
                                        float *d_pi, spl_report_t *rep) {
     if (!c || !d_pi || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
@@ -366,9 +485,18 @@ extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_i
     init.min_iter = 1;
     init.done = 0;
     SPL_CU(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    SPL_CU(cudaMemsetAsync(c->ticket, 0, 2 * sizeof(int), s));
     SPL_CU(cudaMemcpyAsync(c->state, &init, sizeof(ChainState), cudaMemcpyHostToDevice, s));
     const FinishArgs fa = finish_args(c);
     SPL_CU(launch_init_iter(fa, d_warm, s));
+    if (c->mode == SPL_FUSED) {
+        // one cooperative launch runs every step
+        SPL_CU(cudaMemsetAsync(c->run_bar, 0, sizeof(unsigned) * chain_run_bar_words(), s));
+        SPL_CU(cudaMemsetAsync(c->run_ticket, 0, sizeof(int) * c->run_T, s));
+        SPL_CU(launch_chain_run(run_args(c), c->run_grid, s));
+        SPL_CU(cudaMemcpyAsync(c->h_state, c->state, sizeof(ChainState), cudaMemcpyDeviceToHost, s));
+        return chain_report(c, s, d_pi, rep);
+    }
     // Steps are issued in chunks; every kernel exits at once when the device
     // state says done, so over-issuing within a chunk costs only launches.
     const bool graph = chain_graph(c, fa);
@@ -389,6 +517,12 @@ extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_i
         SPL_CU(cudaStreamSynchronize(s));
         if (c->h_state->done || issued >= max_iter) break;
     }
+    return chain_report(c, s, d_pi, rep);
+}
+
+// Error flag, result copy and report of a finished iteration (the state is
+// already being copied to h_state on s).
+static spl_status_t chain_report(spl_chain *c, cudaStream_t s, float *d_pi, spl_report_t *rep) {
     int herr = 0;
     SPL_CU(cudaMemcpyAsync(&herr, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPL_CU(cudaMemcpyAsync(d_pi, c->pi, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, s));
@@ -406,58 +540,87 @@ extern "C" spl_status_t spl_stationary(spl_chain_t *c, double tol, int32_t max_i
     return st;
 }
 
-extern "C" spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass) {
-    if (!c || reps < 1 || !ms_per_pass) return SPL_EINVAL;
+// Times reps dense passes or reps whole steps, replayed from a captured graph
+// (so no host launch overhead), after one untimed replay.
+// Times one persistent fused launch of reps steps (after an untimed launch of
+// a few): the stop rule is held open and max_iter = reps, so the launch makes
+// reps steps plus the one pass its lagged stop decision needs.
+static spl_status_t time_run(spl_chain *c, int32_t reps, float *ms_out) {
     cudaStream_t s = c->stream;
-    // a valid broadcast vector and an unfinished state so no kernel exits early
+    const FinishArgs fa = finish_args(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPL_CU(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        ChainState init{};
+        init.tol_err = 0.f;
+        init.max_iter = r == 0 ? std::min(reps, 4) : reps;
+        init.min_iter = 1 << 30;
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->err_flag, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->run_bar, 0, sizeof(unsigned) * chain_run_bar_words(), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->run_ticket, 0, sizeof(int) * c->run_T, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->state, &init, sizeof(ChainState), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_init_iter(fa, nullptr, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_chain_run(run_args(c), c->run_grid, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "timing");
+    if (herr) return SPL_ETIMEOUT;
+    *ms_out = ms / reps;
+    return SPL_OK;
+}
+
+static spl_status_t time_chain(spl_chain *c, int32_t reps, bool whole_step, float *ms_out) {
+    if (whole_step && c->mode == SPL_FUSED) return time_run(c, reps, ms_out);
+    cudaStream_t s = c->stream;
+    // a valid broadcast vector and a state the stop rule never closes, so
+    // no kernel exits early
     const FinishArgs fa = finish_args(c);
     ChainState init{};
     init.tol_err = 0.f;
     init.max_iter = 1 << 30;
     init.min_iter = 1 << 30;
+    SPL_CU(cudaMemsetAsync(c->ticket, 0, 2 * sizeof(int), s));
     SPL_CU(cudaMemcpyAsync(c->state, &init, sizeof(ChainState), cudaMemcpyHostToDevice, s));
     SPL_CU(launch_init_iter(fa, nullptr, s));
-    cudaEvent_t e0, e1;
-    SPL_CU(cudaEventCreate(&e0));
-    SPL_CU(cudaEventCreate(&e1));
-    spl_status_t st = SPL_OK;
-    for (int i = 0; i < reps + 1 && st == SPL_OK; ++i) {
-        if (i == 1) cudaEventRecord(e0, s);   // first pass is a warm-up
-        if (c->mode == SPL_MATERIALIZED) {
-            GemvArgs g{};
-            g.N = c->N;
-            g.tiles_per_slab = c->tiles_per_slab;
-            g.total_tiles = c->total_tiles;
-            g.tiles_per_cta = c->tiles_per_cta;
-            g.c = c->v;
-            g.part = c->part;
-            g.state = c->state;
-            g.err_flag = c->err_flag;
-            if (launch_gemv(&c->tmap, g, c->gemv_grid, s) != cudaSuccess) st = SPL_ECUDA;
-        } else {
-            TriSplitArgs ta{};
-            ta.N = c->N;
-            ta.vlen = c->vlen;
-            ta.chunk = c->chunk;
-            ta.v = c->v;
-            ta.m = c->w;
-            ta.scal = c->scal;
-            ta.part = c->part;
-            ta.ld_part = c->ld_part;
-            ta.state = c->state;
-            if (launch_tri_split(ta, false, c->chunks, s) != cudaSuccess) st = SPL_ECUDA;
-        }
-    }
-    cudaEventRecord(e1, s);
-    cudaError_t e = cudaEventSynchronize(e1);
+    SPL_CU(cudaStreamSynchronize(s));
+    cudaGraphExec_t exec = nullptr;
+    spl_status_t st = capture_reps(c, fa, reps, whole_step, &exec);
+    if (st != SPL_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);        // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != SPL_OK) return st;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) return cuda_fail(e, "timing");
-    *ms_per_pass = ms / reps;
+    *ms_out = ms / reps;
     return SPL_OK;
+}
+
+extern "C" spl_status_t spl_chain_time_pass(spl_chain_t *c, int32_t reps, float *ms_per_pass) {
+    if (!c || reps < 1 || !ms_per_pass) return SPL_EINVAL;
+    return time_chain(c, reps, false, ms_per_pass);
+}
+
+extern "C" spl_status_t spl_chain_time_step(spl_chain_t *c, int32_t reps, float *ms_per_step) {
+    if (!c || reps < 1 || !ms_per_step) return SPL_EINVAL;
+    return time_chain(c, reps, true, ms_per_step);
 }
 
 extern "C" spl_status_t spl_chain_time_build(spl_chain_t *c, int32_t reps, float *ms_per_build) {

@@ -171,9 +171,10 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // c > cb, "far" for c < cb, and needs a per-entry select only for c == cb.
 // b runs over [b_lo, b_hi); v is indexed by b (callers offset the pointer
 // for a chunk).  All bounds are multiples of 4; the span either starts at or
-// after b_lo, or lies fully below it; a span reaching past b_hi is cut at a
-// 32-entry block boundary (b_hi a multiple of 32 then).
-template <int C, bool kRowPass, int KC = kChain>
+// after b_lo, or lies fully below it (with kLoCut: b_lo may also fall inside
+// the span at a 32-entry block boundary); a span reaching past b_hi is cut at
+// a 32-entry block boundary (b_hi a multiple of 32 then).
+template <int C, bool kRowPass, int KC = kChain, bool kLoCut = false>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
     float acc[C], comp[C];
@@ -188,7 +189,7 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
         tri_run<C, KC>(v, b_lo, min(b_hi, base), m, acc, comp);
     }
     // the span itself (32 C entries, added as chunks of at most kChain)
-    if (base >= b_lo && base < b_hi) {
+    if ((kLoCut ? base + 32 * C > b_lo : base >= b_lo) && base < b_hi) {
         const float4 *v4 = reinterpret_cast<const float4 *>(v);
         float in[kNch][C];
         chains_zero<C>(in);
@@ -201,9 +202,10 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
                 const bool near = kRowPass ? (c < cb) : (c > cb);
                 m[c] = near ? mlo[c] : mhi[c];
             }
-            // blocks past b_hi (only where the span is cut) add nothing
+            // blocks outside [b_lo, b_hi) (only where the span is cut) add nothing
+            const bool in_range = base + 32 * cb < b_hi && (!kLoCut || base + 32 * cb >= b_lo);
 #pragma unroll 2
-            for (int q = 0; q < (base + 32 * cb < b_hi ? 8 : 0); ++q) {
+            for (int q = 0; q < (in_range ? 8 : 0); ++q) {
                 const float4 x = v4[((base + 32 * cb) >> 2) + q];
                 const int t = 4 * q;   // offset of x.x inside the block
 #pragma unroll
@@ -1192,24 +1194,402 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
 }
 
 // ======================================================================
-// Finish kernel of one power step (single CTA)
+// Persistent power iteration of one chain (fused mode)
 // ======================================================================
 //
-// Reduces the partial column sums into y, normalises, forms the step
-// statistics, applies the stop rule, and prepares the next broadcast vector:
+// One cooperative launch (all CTAs resident) runs the steps of one chain
+// with one grid barrier per step.  The column pass is cut into equal work
+// units, (column tile of 128 columns) x (block of 32 rows), in tile-major
+// order; CTA b takes the contiguous units [b U / G, (b+1) U / G), which cover
+// at most a few tiles.  Per step k:
+//   pass        for each tile segment of its units, the CTA stages the rows
+//               of the broadcast vector v (scaled by 1/s of the previous
+//               step) in shared memory, its warps split the rows and sum the
+//               tile's columns over them (the same tile code as the split
+//               pass), the warp partials are added in warp order into one
+//               partial per (CTA, tile), and the last CTA to finish a tile
+//               adds the tile's partials in CTA order into y_j, writes
+//               v_{(j+l) mod N} = y_j rho_{(j+l) mod N} for the next pass and
+//               the tile sum (y, v and the tile sums alternate buffers);
+//   barrier
+//   normalise   every CTA adds the tile sums in a fixed order (s) and, for its
+//               slice of bins, forms pi^(k) = y / s (alternate buffer) and the
+//               step d; its share of the statistics goes to its slot;
+//   decide      on step k-1: every CTA adds the statistics of step k-1 in CTA
+//               order and runs the stop rule on the same numbers, so all CTAs
+//               stop together; pi^(k-1) is then the result.
+// The barrier is a counter of arrivals since launch that one CTA polls before
+// it releases the next generation; every wait is bounded: a CTA that gives up
+// sets err_flag and an abort generation that releases every other waiter,
+// and all CTAs return.
+
+constexpr int kRunNT = 256;
+constexpr int kRunW = kRunNT / 32;
+constexpr int kRunC = 4;
+constexpr int kRunTW = 32 * kRunC;                      // columns per tile (one warp span)
+constexpr int kRunMaxChunk = 8192;                      // rows of v in shared memory at once
+constexpr unsigned kBarAbort = 0xFFFFFFFFu;
+constexpr int kBarGen = 32;                             // index of the generation word
+constexpr uint32_t kGridSpinLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_gpu(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned cas_release_gpu(unsigned *p, unsigned cmp, unsigned v) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(p), "r"(cmp), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int add_acq_rel_gpu(int *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Grid-wide barrier over a cooperative launch.  bar[0] counts arrivals since
+// launch, bar[kBarGen] (another 128-byte line) is the released generation;
+// gen is the calling CTA's count of barriers passed (thread 0's copy is the
+// one used).  False if the grid was aborted.
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        const unsigned next = gen + 1u;
+        red_release_add_gpu(&bar[0], 1u);
+        if (blockIdx.x == 0) {
+            const unsigned target = next * gridDim.x;
+            uint32_t spins = 0;
+            while ((int)(ld_acquire_gpu(&bar[0]) - target) < 0) {
+                if (++spins > kGridSpinLimit) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok) {
+                ok = cas_release_gpu(&bar[kBarGen], gen, next) == gen;
+            } else {
+                atomicExch(err_flag, 1);
+                atomicExch(&bar[kBarGen], kBarAbort);
+            }
+        } else {
+            unsigned g;
+            uint32_t spins = 0;
+            while ((g = ld_acquire_gpu(&bar[kBarGen])) == gen) {
+                if (++spins > kGridSpinLimit) {
+                    atomicExch(err_flag, 1);
+                    atomicExch(&bar[kBarGen], kBarAbort);
+                    g = kBarAbort;
+                    break;
+                }
+            }
+            ok = g != kBarAbort;
+        }
+        gen = next;
+        *s_flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// First unit of CTA b, and the CTA that owns unit u.
+__device__ __forceinline__ long long run_unit0(int b, long long U, int G) { return (long long)b * U / G; }
+__device__ __forceinline__ int run_owner(long long u, long long U, int G) {
+    return (int)(((u + 1) * G + U - 1) / U) - 1;
+}
+
+// End of a tile segment of one CTA: the warp partials added in warp order.
+// A tile the CTA covers whole is finished here (y, v and the tile sum, as in
+// run_tile_reduce); a shared tile leaves the CTA's partial in its slot.
+__device__ __forceinline__ void run_flush(const ChainRunArgs &a, int t, int t_first, int b, bool own_first,
+                                          bool own_last, int t_last, const float (&acc)[kRunC],
+                                          float (*wred)[kRunTW], float *red, float *ydst, float *vdst,
+                                          float *tdst) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, N = a.N;
+#pragma unroll
+    for (int c = 0; c < kRunC; ++c) wred[wid][32 * c + lane] = acc[c];
+    __syncthreads();
+    const bool owned = (t != t_first || own_first) && (t != t_last || own_last);
+    float p = 0.f;
+    if (tid < kRunTW) {
+#pragma unroll
+        for (int w = 0; w < kRunW; ++w) p += wred[w][tid];
+    }
+    if (!owned) {
+        if (tid < kRunTW) a.part[((size_t)b * a.segs + (t - t_first)) * kRunTW + tid] = p;
+    } else {
+        const int col = t * kRunTW + tid;
+        if (tid >= kRunTW || col >= N) p = 0.f;
+        if (tid < kRunTW && col < N) {
+            ydst[col] = p;
+            int r = col + a.l;
+            r -= (r >= N) ? N : 0;
+            vdst[r] = p * __ldg(a.rho + r);
+        }
+        const float tsb = block_sum<kRunNT>(p, red);
+        if (tid == 0) tdst[t] = tsb;
+    }
+    __syncthreads();   // wred and red are reused
+}
+
+// Adds the tile's partials in CTA order (CTA bf may have started in an
+// earlier tile; every later CTA of the tile starts inside it, slot 0) into
+// y_j, writes v_{(j+l) mod N} = y_j rho_{(j+l) mod N} and the tile sum.
+__device__ __forceinline__ void run_tile_reduce(const ChainRunArgs &a, int t, long long U, int G, float *ydst,
+                                                float *vdst, float *tdst, float *red) {
+    const int tid = threadIdx.x, N = a.N, RB = a.RB;
+    const int bf = run_owner((long long)t * RB, U, G), bl = run_owner((long long)(t + 1) * RB - 1, U, G);
+    const int col = t * kRunTW + tid;
+    float yv = 0.f;
+    if (tid < kRunTW && col < N) {
+        int r = col + a.l;
+        r -= (r >= N) ? N : 0;
+        const float rr = __ldg(a.rho + r);
+        const float *pp = a.part + tid;
+        yv = __ldcg(pp + ((size_t)bf * a.segs + (t - (int)(run_unit0(bf, U, G) / RB))) * kRunTW);
+#pragma unroll 8
+        for (int bb = bf + 1; bb <= bl; ++bb) yv += __ldcg(pp + (size_t)bb * a.segs * kRunTW);
+        ydst[col] = yv;
+        vdst[r] = yv * rr;
+    }
+    const float tsb = block_sum<kRunNT>(yv, red);
+    if (tid == 0) tdst[t] = tsb;
+}
+
+__global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
+    extern __shared__ float4 smem4[];
+    float *sv = reinterpret_cast<float *>(smem4);
+    __shared__ float wred[kRunW][kRunTW];
+    __shared__ float red[5 * kRunW + 5];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int N = a.N, T = a.T, RB = a.RB;
+    const size_t vlen = (size_t)a.vlen;
+    const long long U = (long long)T * RB;
+    const long long u0 = run_unit0(b, U, G), u1 = run_unit0(b + 1, U, G);
+    const int t_first = (int)(u0 / RB), t_last = (int)((u1 - 1) / RB);
+    // tiles this CTA covers whole have no other contributor
+    const bool own_first = u0 == (long long)t_first * RB && u1 >= (long long)(t_first + 1) * RB;
+    const bool own_last = u1 == (long long)(t_last + 1) * RB && u0 <= (long long)t_last * RB;
+    const float eL = (float)a.scal[1];
+    ChainState *stp = a.state;
+    StopState st = stp->st;                 // every CTA keeps the same copy
+    const float tol_err = stp->tol_err;
+    const int min_iter = stp->min_iter, max_iter = stp->max_iter;
+    unsigned gen = 0u;
+    // this CTA's slice of bins for the normalisation
+    const int S = (N + G - 1) / G;
+    const int j0 = min(N, b * S), j1 = min(N, j0 + S);
+    const float *vsrc = a.v0;               // h^(0) = pi^(0)_{(k-l) mod N} rho_k
+    float inv = 1.f;
+    // arrivals expected at the shared first and last tiles, less one
+    const int cnt_first = run_owner((long long)(t_first + 1) * RB - 1, U, G) - run_owner((long long)t_first * RB, U, G);
+    const int cnt_last = run_owner((long long)(t_last + 1) * RB - 1, U, G) - run_owner((long long)t_last * RB, U, G);
+    for (int k = 1;; ++k) {
+        float *ydst = a.y + (k & 1) * vlen;
+        float *vdst = a.vb + (k & 1) * vlen;
+        float *tdst = a.tsum + (size_t)(k & 1) * T;
+        // ---- pass k, in windows of at most kRunMaxChunk rows staged in unit order
+        int cur_t = t_first;
+        float mlo[kRunC], mhi[kRunC], acc[kRunC];
+        // the first tile's column factors load with the staging
+#pragma unroll
+        for (int c = 0; c < kRunC; ++c) {
+            const int col = t_first * kRunTW + 32 * c + lane;
+            const float m = col < N ? __ldg(a.w + col) : 0.f;
+            mlo[c] = m;
+            mhi[c] = m * eL;
+            acc[c] = 0.f;
+        }
+        for (long long wu0 = u0; wu0 < u1; wu0 += kRunMaxChunk / 32) {
+            const long long wu1 = min(u1, wu0 + kRunMaxChunk / 32);
+            const int tw0 = (int)(wu0 / RB);
+            const int off0 = (int)(wu0 - (long long)tw0 * RB);
+            const int nq = (int)(wu1 - wu0) * 8;
+            const float4 *v4 = reinterpret_cast<const float4 *>(vsrc);
+            float4 *s4 = reinterpret_cast<float4 *>(sv);
+            for (int q = tid; q < nq; q += kRunNT) {
+                int o = off0 + (q >> 3);
+                o -= (o / RB) * RB;                     // 32-row block inside its tile
+                float4 x = __ldcg(v4 + o * 8 + (q & 7));
+                x.x *= inv;
+                x.y *= inv;
+                x.z *= inv;
+                x.w *= inv;
+                s4[q] = x;
+            }
+            __syncthreads();
+            for (int t = tw0; (long long)t * RB < wu1; ++t) {
+                const long long su0 = max(wu0, (long long)t * RB), su1 = min(wu1, (long long)(t + 1) * RB);
+                if (t != cur_t) {
+                    run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, red, ydst, vdst, tdst);
+#pragma unroll
+                    for (int c = 0; c < kRunC; ++c) {
+                        const int col = t * kRunTW + 32 * c + lane;
+                        const float m = col < N ? __ldg(a.w + col) : 0.f;
+                        mlo[c] = m;
+                        mhi[c] = m * eL;
+                        acc[c] = 0.f;
+                    }
+                    cur_t = t;
+                }
+                // warp wid takes 32-row blocks [wb0, wb1) of the segment
+                const int rb0 = (int)(su0 - (long long)t * RB), rb1 = (int)(su1 - (long long)t * RB);
+                const int nb = rb1 - rb0;
+                const int wb0 = rb0 + (nb * wid) / kRunW, wb1 = rb0 + (nb * (wid + 1)) / kRunW;
+                if (wb1 > wb0) {
+                    const float *vt = sv + ((long long)t * RB - wu0) * 32;   // row r of tile t at vt[r]
+                    float out[kRunC];
+                    tri_pass<kRunC, false, kChain, true>(vt, 32 * wb0, 32 * wb1, t * kRunTW, lane, mlo, mhi, out);
+#pragma unroll
+                    for (int c = 0; c < kRunC; ++c) acc[c] += out[c];
+                }
+            }
+            __syncthreads();   // sv is restaged
+        }
+        run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, red, ydst, vdst, tdst);
+        // shared tiles: the last CTA to finish one adds its partials
+        __syncthreads();
+        if (tid == 0) {
+            int old0 = -1, old1 = -1;
+            __threadfence();
+            if (!own_first) old0 = atomicAdd(a.tile_ticket + t_first, 1);
+            if (t_last != t_first && !own_last) old1 = atomicAdd(a.tile_ticket + t_last, 1);
+            const bool last0 = old0 >= 0 && old0 == cnt_first;
+            const bool last1 = old1 >= 0 && old1 == cnt_last;
+            if (last0) a.tile_ticket[t_first] = 0;
+            if (last1) a.tile_ticket[t_last] = 0;
+            if (last0 || last1) __threadfence();
+            s_flag = (last0 ? 1 : 0) | (last1 ? 2 : 0);
+        }
+        __syncthreads();
+        const int lastmask = s_flag;
+        if (lastmask & 1) run_tile_reduce(a, t_first, U, G, ydst, vdst, tdst, red);
+        if (lastmask & 2) {
+            __syncthreads();   // red is reused
+            run_tile_reduce(a, t_last, U, G, ydst, vdst, tdst, red);
+        }
+        if (!grid_sync(a.bar, gen, a.err_flag, &s_flag)) {
+            if (b == 0) {
+                stp->st = st;
+                stp->done = 1;
+                stp->status = ST_ENOCONV;
+            }
+            return;
+        }
+        // ---- normalise step k, and decide on step k-1
+        float *pcur = (k & 1) ? a.pi_alt : a.pi;
+        const float *pprev = (k & 1) ? a.pi : a.pi_alt;
+        // every load first: statistics of step k-1, tile sums, own bins
+        float red5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (k >= 2) {
+            const float4 *bs = reinterpret_cast<const float4 *>(a.blk + (size_t)((k - 1) & 1) * G * 4);
+            // G is at most 2 kRunNT (two CTAs per SM): both loads in flight
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x0 = tid < G ? __ldcg(bs + tid) : z;
+            const float4 x1 = tid + kRunNT < G ? __ldcg(bs + tid + kRunNT) : z;
+            red5[0] = x0.x + x1.x;
+            red5[1] = x0.y + x1.y;
+            red5[2] = x0.z + x1.z;
+            red5[3] = x0.w + x1.w;
+        }
+        for (int t = tid; t < T; t += kRunNT) red5[4] += __ldcg(tdst + t);
+        const int jf = j0 + tid;
+        float fy = 0.f, fp = 0.f, f1 = 0.f, f2 = 0.f;
+        if (jf < j1) {
+            fy = __ldcg(ydst + jf);
+            fp = pprev[jf];
+            f1 = a.d1[jf];
+            f2 = a.d2[jf];
+        }
+        block_sum_k<kRunNT, 5>(red5, red);
+        inv = 1.f / red5[4];
+        if (tid == 0) {
+            int fin = 0;
+            if (k >= 2) {
+                const int su = stop_update(st, red5[0], red5[1], red5[2], red5[3], tol_err, min_iter);
+                if (su != STOP_CONTINUE) fin = su == STOP_CONVERGED ? 1 : 2;
+                else if (st.k >= max_iter) fin = 2;
+                if (fin && b == 0) {
+                    stp->st = st;
+                    stp->done = 1;
+                    stp->status = fin == 1 ? ST_OK : ST_ENOCONV;
+                }
+            }
+            s_flag = fin;
+        }
+        float stats[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = jf; j < j1; j += kRunNT) {
+            if (j != jf) {
+                fy = __ldcg(ydst + j);
+                fp = pprev[j];
+                f1 = a.d1[j];
+                f2 = a.d2[j];
+            }
+            const float pn = fy * inv;
+            const float d = pn - fp;
+            stats[0] += fabsf(d);
+            stats[1] = fmaf(d, d, stats[1]);
+            stats[2] = fmaf(d, f1, stats[2]);
+            stats[3] = fmaf(d, f2, stats[3]);
+            a.d2[j] = f1;
+            a.d1[j] = d;
+            pcur[j] = pn;
+        }
+        block_sum_k<kRunNT, 4>(stats, red);   // its barriers also publish s_flag
+        if (s_flag) {
+            // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
+            if ((k - 1) & 1)
+                for (int j = j0 + tid; j < j1; j += kRunNT) a.pi[j] = a.pi_alt[j];
+            return;
+        }
+        if (tid == 0)
+            reinterpret_cast<float4 *>(a.blk + (size_t)(k & 1) * G * 4)[b] =
+                make_float4(stats[0], stats[1], stats[2], stats[3]);
+        vsrc = vdst;
+    }
+}
+
+// ======================================================================
+// Finish of one power step (whole GPU, two kernels)
+// ======================================================================
+//
+// Stage 1 reduces the dense pass's partial column sums into y and sums y;
+// stage 2 normalises, forms the step statistics, applies the stop rule and
+// prepares the next broadcast vector:
 //   materialised: c_i = pi_i / r_i           (row space)
 //   fused:        h_k = pi_{(k-l) mod N} rho_k  (p-space)
+// Each stage's grid-wide sum goes through per-CTA partials that the last CTA
+// to arrive (an atomic ticket) adds in CTA order: the result does not depend
+// on which CTA finishes last, and no CTA ever waits for another.
+
+constexpr int kFinishNT = 256;
+
+// Publishes this CTA's partials (written by thread 0 before the call) and
+// tells whether it is the last CTA of the grid to do so.
+__device__ __forceinline__ bool arrive_last(int *ticket, bool *s_last) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    return *s_last;
+}
 
 template <int NT>
-__global__ void __launch_bounds__(NT) finish_step_kernel(FinishArgs a) {
-    __shared__ float red[8 * (NT / 32) + 8];
+__global__ void __launch_bounds__(NT) reduce_parts_kernel(FinishArgs a) {
+    __shared__ float red[NT / 32 + 1];
+    __shared__ bool s_last;
     ChainState *stp = a.state;
     if (stp->done) return;
-    const int N = a.N;
-    const int tid = threadIdx.x;
-    float ysum = 0.f;
-    for (int j = tid; j < N; j += NT) {
-        float y = 0.f;
+    const int j = blockIdx.x * NT + threadIdx.x;
+    float y = 0.f;
+    if (j < a.N) {
         if (a.mode == 0) {
             // materialised: partials per (cta, slot)
             const int slab = j / kGemvCols, t = j - slab * kGemvCols;
@@ -1223,47 +1603,81 @@ __global__ void __launch_bounds__(NT) finish_step_kernel(FinishArgs a) {
             for (int q = 0; q < a.nparts; ++q) y += a.part[(size_t)q * a.ld_part + j];
         }
         a.y[j] = y;
-        ysum += y;
     }
-    const float s = block_sum<NT>(ysum, red);
-    const float inv = 1.f / s;
+    const float bs = block_sum<NT>(y, red);
+    if (threadIdx.x == 0) a.blk[blockIdx.x] = bs;
+    if (!arrive_last(a.ticket, &s_last)) return;
+    float t = 0.f;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) t += __ldcg(a.blk + b);
+    const float sum = block_sum<NT>(t, red);
+    if (threadIdx.x == 0) {
+        stp->ysum = sum;
+        a.ticket[0] = 0;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) normalize_step_kernel(FinishArgs a) {
+    __shared__ float red[4 * (NT / 32) + 4];
+    __shared__ bool s_last;
+    ChainState *stp = a.state;
+    if (stp->done) return;
+    const int N = a.N;
+    const float inv = 1.f / stp->ysum;
+    const int j = blockIdx.x * NT + threadIdx.x;
     float stats[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int j = tid; j < N; j += NT) {
+    if (j < N) {
         const float pn = a.y[j] * inv;
         const float d = pn - a.pi[j];
         const float e1 = a.d1[j], e2 = a.d2[j];
-        stats[0] += fabsf(d);
-        stats[1] = fmaf(d, d, stats[1]);
-        stats[2] = fmaf(d, e1, stats[2]);
-        stats[3] = fmaf(d, e2, stats[3]);
+        stats[0] = fabsf(d);
+        stats[1] = d * d;
+        stats[2] = d * e1;
+        stats[3] = d * e2;
         a.d2[j] = e1;
         a.d1[j] = d;
         a.pi[j] = pn;
     }
-    block_sum_k<NT, 4>(stats, red);
-    StopState st = stp->st;
-    const int su = stop_update(st, stats[0], stats[1], stats[2], stats[3], stp->tol_err, stp->min_iter);
-    const bool stop = su != STOP_CONTINUE;
-    __syncthreads();
-    if (tid == 0) {
-        stp->st = st;
-        if (stop) { stp->done = 1; stp->status = su == STOP_CONVERGED ? ST_OK : ST_ENOCONV; }
-        else if (st.k >= stp->max_iter) { stp->done = 1; stp->status = ST_ENOCONV; }
-    }
-    if (stop) return;
-    // next broadcast vector
-    for (int k = tid; k < a.vlen; k += NT) {
+    if (j < a.vlen) {
+        // next broadcast vector, from y (pi of another index may not be
+        // written yet); y_i * inv is the same number as the new pi_i
         float h = 0.f;
-        if (k < N) {
+        if (j < N) {
             if (a.mode == 0) {
-                h = a.pi[k] / a.rowsum[k];
+                h = (a.y[j] * inv) / a.rowsum[j];
             } else {
-                int i = k - a.l;
+                int i = j - a.l;
                 i += (i < 0) ? N : 0;
-                h = a.pi[i] * a.rho[k];
+                h = (a.y[i] * inv) * a.rho[j];
             }
         }
-        a.v[k] = h;
+        a.v[j] = h;
+    }
+    block_sum_k<NT, 4>(stats, red);
+    float *blk = a.blk + gridDim.x;     // stage 1 used the first gridDim.x (at most) floats
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) blk[4 * blockIdx.x + k] = stats[k];
+    }
+    if (!arrive_last(a.ticket + 1, &s_last)) return;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] += __ldcg(blk + 4 * b + k);
+    }
+    block_sum_k<NT, 4>(t, red);
+    if (threadIdx.x == 0) {
+        StopState st = stp->st;
+        const int su = stop_update(st, t[0], t[1], t[2], t[3], stp->tol_err, stp->min_iter);
+        stp->st = st;
+        if (su != STOP_CONTINUE) {
+            stp->done = 1;
+            stp->status = su == STOP_CONVERGED ? ST_OK : ST_ENOCONV;
+        } else if (st.k >= stp->max_iter) {
+            stp->done = 1;
+            stp->status = ST_ENOCONV;
+        }
+        a.ticket[1] = 0;
     }
 }
 
@@ -1475,9 +1889,40 @@ cudaError_t launch_finish_rows(int N, int nparts, int ld_part, const float *part
 }
 
 cudaError_t launch_finish_step(const FinishArgs &a, cudaStream_t s) {
-    finish_step_kernel<1024><<<1, 1024, 0, s>>>(a);
+    const int g1 = (a.N + kFinishNT - 1) / kFinishNT;
+    const int g2 = (a.vlen + kFinishNT - 1) / kFinishNT;   // vlen >= N
+    reduce_parts_kernel<kFinishNT><<<g1, kFinishNT, 0, s>>>(a);
+    normalize_step_kernel<kFinishNT><<<g2, kFinishNT, 0, s>>>(a);
     return cudaGetLastError();
 }
+
+int chain_run_tile_cols() { return kRunTW; }
+int chain_run_bar_words() { return 2 * kBarGen; }
+int chain_run_max_grid() { return 2 * kRunNT; }
+int chain_run_max_chunk() { return kRunMaxChunk; }
+size_t chain_run_smem_bytes(int chunk) { return (size_t)chunk * sizeof(float); }
+
+int chain_run_blocks_per_sm(int chunk) {
+    const size_t smem = chain_run_smem_bytes(chunk);
+    if (cudaFuncSetAttribute(chain_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chain_run_kernel, kRunNT, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = chain_run_smem_bytes(a.chunk);
+    cudaError_t e = cudaFuncSetAttribute(chain_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ChainRunArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(chain_run_kernel), dim3(grid), dim3(kRunNT),
+                                       params, smem, s);
+}
+
+size_t finish_blk_floats(int vlen) { return 5 * (size_t)((vlen + kFinishNT - 1) / kFinishNT); }
 
 cudaError_t launch_init_iter(const FinishArgs &a, const float *warm, cudaStream_t s) {
     init_iter_kernel<1024><<<1, 1024, 0, s>>>(a, warm);

@@ -21,7 +21,8 @@ struct ChainState {
     float tol_err;
     int32_t max_iter;
     int32_t min_iter;
-    int32_t pad_[3];
+    float ysum;              // sum of the current step's y (finish stage 1 -> 2)
+    int32_t pad_[2];
 };
 
 struct BatchArgs {
@@ -68,6 +69,42 @@ struct TriSplitArgs {
     const ChainState *state; // may be NULL
 };
 
+// Persistent power iteration of one chain (fused mode): one cooperative
+// launch runs every step.  The column pass is cut into T x RB equal units,
+// (tile of chain_run_tile_cols() columns) x (32 rows), taken by the CTAs in
+// contiguous ranges; each CTA leaves one partial per tile it touches, and the
+// last CTA to finish a tile adds the tile's partials.
+struct ChainRunArgs {
+    int N, vlen, l;
+    int T, RB;               // column tiles; 32-row blocks per tile (vlen / 32)
+    int segs;                // partial slots per CTA (tiles one CTA's units may touch)
+    int chunk;               // rows of h staged in shared memory at once (at most)
+    const float *w;          // [vlen] column factors w_j (zero past N)
+    const double *scal;      // [1] = e^{-Lambda}
+    const float *rho;        // [vlen] rho_k = u_k / r'_k
+    const float *v0;         // [vlen] first broadcast vector pi^(0)_{(k-l) mod N} rho_k, zero past N
+    float *pi, *pi_alt;      // [N] iterates of even and odd steps (pi: pi^(0) in, the result out)
+    float *d1, *d2;          // [N] the last two steps
+    float *y;                // [2][vlen] unnormalised iterates (alternating)
+    float *vb;               // [2][vlen] next broadcast vectors (alternating), zero past N
+    float *tsum;             // [2][T] tile sums of y
+    float *part;             // [grid][segs][tile columns] per-CTA partial column sums
+    float *blk;              // [2][grid][4] per-CTA step statistics (16-byte aligned)
+    int *tile_ticket;        // [T] arrival counters, zero between uses
+    unsigned *bar;           // [chain_run_bar_words()] grid barrier words (zero at launch)
+    ChainState *state;
+    int *err_flag;           // set if a CTA gave up waiting at the barrier
+};
+
+int chain_run_tile_cols();
+int chain_run_bar_words();
+int chain_run_max_grid();
+int chain_run_max_chunk();
+size_t chain_run_smem_bytes(int chunk);
+// CTAs per SM the cooperative launch can keep resident (0 on error).
+int chain_run_blocks_per_sm(int chunk);
+cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s);
+
 struct FinishArgs {
     int mode;                // 0 materialised (GEMV partials), 1 fused (split partials)
     int N, l;
@@ -82,6 +119,8 @@ struct FinishArgs {
     const float *rho;        // fused: u_k / r'_k
     float *v;                // next broadcast vector
     ChainState *state;
+    float *blk;              // per-CTA partial sums of the finish stages [finish_blk_floats(vlen)]
+    int *ticket;             // [2] CTA arrival counters of the finish stages, zero between launches
 };
 
 struct SpectralArgs {
@@ -121,6 +160,7 @@ cudaError_t launch_tri_split(const TriSplitArgs &a, bool row_pass, int chunks, c
 cudaError_t launch_finish_rows(int N, int nparts, int ld_part, const float *part, const float *u, float *rho,
                                float *rowsum_p, int l, cudaStream_t s);
 cudaError_t launch_finish_step(const FinishArgs &a, cudaStream_t s);
+size_t finish_blk_floats(int vlen);
 cudaError_t launch_init_iter(const FinishArgs &a, const float *warm, cudaStream_t s);
 
 }  // namespace spl

@@ -55,7 +55,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
-            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass",
+            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
 
 _lib = None
@@ -149,6 +149,8 @@ def lib():
         L.spl_chain_time_build.restype = ctypes.c_int
         L.spl_chain_time_pass.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.spl_chain_time_pass.restype = ctypes.c_int
+        L.spl_chain_time_step.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
+        L.spl_chain_time_step.restype = ctypes.c_int
         L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         L.spl_gemm_bf16.restype = ctypes.c_int
         _lib = L
@@ -231,6 +233,12 @@ class Chain:
         """Device ms of one dense power-step pass (spl_chain_time_pass)."""
         ms = ctypes.c_float()
         _check(lib().spl_chain_time_pass(self._c, int(reps), ctypes.byref(ms)), "spl_chain_time_pass")
+        return float(ms.value)
+
+    def time_step(self, reps: int = 20) -> float:
+        """Device ms of one whole power step (spl_chain_time_step)."""
+        ms = ctypes.c_float()
+        _check(lib().spl_chain_time_step(self._c, int(reps), ctypes.byref(ms)), "spl_chain_time_step")
         return float(ms.value)
 
     def time_build(self, reps: int = 10) -> float:

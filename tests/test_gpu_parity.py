@@ -162,6 +162,25 @@ def test_highres_materialized_and_fused(spl, t_d):
         ch.close()
 
 
+def test_chain_timing_leaves_chain_usable_and_results_repeat(spl):
+    """The finish stages add their per-CTA partials in CTA order whichever
+    CTA arrives last: a chain gives the same pmf bit for bit on every call,
+    also after the graph-timed passes and steps (which reset its iterate)."""
+    px = W.pixel(3000, 75.0, 30.0, 0.5, 0.5, 0.5)
+    p = _dict(px)
+    ref = oracle.stationary(p, shift=oracle.shift_l(p))
+    for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
+        ch = spl.Chain(px, mode)
+        pi1, r1 = ch.stationary(tol=1e-6)
+        pi1 = pi1.cpu().numpy()
+        assert ch.time_pass(5) > 0.0 and ch.time_step(5) > 0.0
+        pi2, r2 = ch.stationary(tol=1e-6)
+        np.testing.assert_array_equal(pi2.cpu().numpy(), pi1)
+        assert r1["iters"] == r2["iters"] and r2["status"] == 0
+        assert _l1(pi1, ref) < L1_TOL
+        ch.close()
+
+
 def test_pure_background_uniform(spl):
     px = W.pixel(999, 33.3, 30.0, 0.5, 0.0, 2.0)
     for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
