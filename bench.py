@@ -607,7 +607,7 @@ def main():
     ap.add_argument("--mc-cycles", type=int, default=50000, help="laser cycles per Monte Carlo run")
     ap.add_argument("--audit", type=int, default=512, help="pixels of the timed output checked against the oracle")
     ap.add_argument("--train-pixels", type=int, default=200_000)
-    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--epochs", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -150,3 +150,31 @@ def test_learned_start_with_structured_step(spl):
     for r, k in enumerate(idx):
         assert np.abs(s[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() < 1e-6
     net.close()
+
+
+def test_headline_launch_array256_learned_sampled(spl):
+    """The launch the benchmark times: the 256 x 256 array (65536 pixels,
+    N = 2000) with the learned start in one persistent launch, the launch
+    configuration chosen by the autotuner; 32 pixels sampled by seed against
+    the FP64 oracle, every pmf normalised, every pixel converged."""
+    train = W.training(16384, seed=2)
+    tgt, _, _ = spl.batch_stationary(train, tol=1e-6)
+    tgt = tgt.view(len(train), 2000)
+    net = spl.MLP(max_batch=65536, seed=1)
+    c_all = [spl.pixels_to_c(train[i:i + 4096]) for i in range(0, len(train), 4096)]
+    step = 0
+    for epoch in range(10):
+        for b, cpx in enumerate(c_all):
+            net.train_step(cpx, 4096, tgt[b * 4096:(b + 1) * 4096], lr=3e-3 * min(1.0, (step + 1) / 20))
+            step += 1
+    px = W.array256()
+    out, off, reps = net.batch_stationary(px, tol=1e-6)
+    assert np.all(reps["status"] == 0)
+    o = out.cpu().numpy().astype(np.float64)
+    sums = np.add.reduceat(o, off[:-1])
+    assert np.abs(sums - 1).max() < 1e-5
+    idx = W.sample_indices(len(px), 32, seed=34)
+    refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
+    worst = max(np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() for r, k in enumerate(idx))
+    assert worst < 1e-6, worst
+    net.close()

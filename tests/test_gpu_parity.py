@@ -181,6 +181,59 @@ def test_chain_timing_leaves_chain_usable_and_results_repeat(spl):
         ch.close()
 
 
+def test_fused_chain_multiwindow_vs_oracle(spl):
+    """N = 18000: each CTA of the persistent fused iteration holds more rows
+    than one shared-memory window (262 units of 32 rows > 256) and covers two
+    column tiles; dead time longer than the period (t_d = 130 > t_r)."""
+    px = W.pixel(18000, 130.0, 30.0, 0.3, 0.5, 0.5)
+    p = _dict(px)
+    ref = oracle.batch_stationary([p], tol=1e-12)[0]
+    ch = spl.Chain(px, spl.SPL_FUSED)
+    pi, rep = ch.stationary(tol=1e-6, max_iter=500)
+    assert rep["status"] == 0
+    assert _l1(pi.cpu().numpy(), ref) < L1_TOL, (_l1(pi.cpu().numpy(), ref), rep)
+    ch.close()
+
+
+def test_tune_cache_file_is_read(tmp_path):
+    """SPL_TUNE_CACHE: a process that finds an entry for its batch kind uses
+    it instead of measuring (the file gains no line) and gives the same pmfs
+    bit for bit as the process that measured and wrote it."""
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = (
+        "import json, sys, numpy as np\n"
+        "from paper_2509_20500_gb300 import spl, workloads as W\n"
+        "px = W.array_pixels(1200, seed=81)\n"
+        "out, off, _ = spl.batch_stationary(px)\n"
+        "np.save(sys.argv[1], out.cpu().numpy())\n"
+        "print(json.dumps(spl.batch_tune_lookup(2000)))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPL_TUNE_CACHE=str(cache), PYTHONPATH=root)
+
+    def run(tag):
+        r = subprocess.run([sys.executable, "-c", code, str(tmp_path / f"{tag}.npy")], cwd=root, env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return r.stdout.strip().splitlines()[-1]
+
+    first = run("a")
+    lines = cache.read_text().split("\n")
+    lines = [x for x in lines if x.strip()]
+    assert len(lines) == 1
+    key, val = lines[0].split()[:3], [int(x) for x in lines[0].split()[3:]]
+    assert val[0] == 256 and first == "[%d, %d, %d]" % tuple(val)
+    # another valid configuration for the same key: level 0 (or 2), one block per SM
+    alt = [256, 0 if val[1] != 0 else 2, 1]
+    cache.write_text(" ".join(key + [str(x) for x in alt]) + "\n")
+    second = run("b")
+    assert second == "[%d, %d, %d]" % tuple(alt)
+    assert len([x for x in cache.read_text().split("\n") if x.strip()]) == 1
+    np.testing.assert_array_equal(np.load(tmp_path / "a.npy"), np.load(tmp_path / "b.npy"))
+
+
 def test_pure_background_uniform(spl):
     px = W.pixel(999, 33.3, 30.0, 0.5, 0.0, 2.0)
     for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
