@@ -41,21 +41,26 @@ constexpr int kLayers = 5;      // 4 hidden + output
 constexpr int kOut = 2000;      // bins of the learned frame
 constexpr int kOutPad = 2048;
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
-constexpr uint32_t kTileBytes = BM * BK * 2;          // 16 KB (A or B tile)
-constexpr uint32_t kStageBytes = 2 * kTileBytes;
-constexpr uint32_t kTmemCols = BN;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr uint32_t kTileBytesA = BM * BK * 2;         // 16 KB
+constexpr uint32_t kTileBytesB = BN * BK * 2;         // 32 KB
+constexpr uint32_t kStageBytes = kTileBytesA + kTileBytesB;
+constexpr uint32_t kTmemCols = 2 * BN;                // two accumulators: the epilogue of one tile
+                                                      // overlaps the MMAs of the next
 constexpr size_t kGemmSmem = (size_t)STAGES * kStageBytes + 1024;
-// 8 warps: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs, and
-// all eight run the epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
-// lane quadrant a warp may access) and accumulator columns 64 (w / 4) .. + 63.
-constexpr int kGemmThreads = 256;
+// 12 warps, persistent (one CTA per SM, tiles strided over the grid):
+// warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs, warp 2 owns the
+// TMEM allocation, and warps 4..11 run the epilogue: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (the lane quadrant a warp may access) and accumulator
+// columns 128 ((w - 4) / 4) .. + 127.
+constexpr int kGemmThreads = 384;
+constexpr int kEpiWarp0 = 4, kEpiWarps = 8;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 enum : int { EPI_GELU = 0, EPI_LOGITS = 1, EPI_DGELU = 2, EPI_F32 = 3 };
 
 struct GemmArgs {
-    int M, N, K;                       // M % 128 == 0, K % 64 == 0, N <= grid.y * 128
+    int M, N, K;                       // M % 128 == 0, K % 64 == 0, N % 32 == 0 (N tiles of 256)
     const float *bias;                 // [N]
     __nv_bfloat16 *out_bf16;           // [M][ld] row-major
     __nv_bfloat16 *out_bf16_t;         // [N][M] transposed, may be NULL
@@ -74,35 +79,36 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 
 // D[M x N] = A[M x K] * B[N x K]^T, both operands K-major BF16.
 template <int MODE>
-__global__ void __launch_bounds__(kGemmThreads, 2) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                                    const __grid_constant__ CUtensorMap tb, GemmArgs g) {
     extern __shared__ uint8_t gemm_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[STAGES];
     __shared__ __align__(8) uint64_t empty_bar[STAGES];
-    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ __align__(8) uint64_t tfull_bar[2];
+    __shared__ __align__(8) uint64_t tempty_bar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ float s_bias[BN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // N tiles vary fastest, so the CTAs that share an A tile (one 128-row
-    // slice of the activations) run together and read it once from HBM
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KB = g.K / BK;
-    if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
-        for (int c = threadIdx.x; c < BN; c += kGemmThreads) s_bias[c] = (n0 + c < g.N) ? g.bias[n0 + c] : 0.f;
-    }
+    // tiles in row-major order of (M tile, N tile): the CTAs running at one
+    // time share A tiles (one 128-row slice of the activations) through L2
+    const int n_tiles = (g.N + BN - 1) / BN;
+    const int total = (g.M / BM) * n_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             umma::mbar_init(&full_bar[s], 1);
             umma::mbar_init(&empty_bar[s], 1);
         }
-        umma::mbar_init(&acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&tfull_bar[b], 1);
+            umma::mbar_init(&tempty_bar[b], kEpiWarps);
+        }
         umma::fence_barrier_init();
         umma::prefetch_tmap(&ta);
         umma::prefetch_tmap(&tb);
     }
-    if (warp == 0) {
+    if (warp == 2) {
         umma::tmem_alloc(&tmem_base, kTmemCols);
         umma::tmem_relinquish();
     }
@@ -113,108 +119,140 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_bf16_kernel(const __grid
 
     bool ok = true;
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !umma::mbar_wait(&empty_bar[s], (uint32_t)(((kb / STAGES) - 1) & 1), kWaitLimit)) {
-                ok = false;
-                break;
+        // TMA producer: a ring of STAGES (A, B) k-blocks across all tiles
+        uint32_t it = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const uint32_t s = it % STAGES;
+                if (it >= STAGES && !umma::mbar_wait(&empty_bar[s], ((it / STAGES) - 1) & 1, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *st = smem + (size_t)s * kStageBytes;
+                umma::mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+                umma::tma_load_2d(st, &ta, &full_bar[s], kb * BK, m0);
+                umma::tma_load_2d(st + kTileBytesA, &tb, &full_bar[s], kb * BK, n0);
             }
-            uint8_t *st = smem + (size_t)s * kStageBytes;
-            umma::mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-            umma::tma_load_2d(st, &ta, &full_bar[s], kb * BK, m0);
-            umma::tma_load_2d(st + kTileBytes, &tb, &full_bar[s], kb * BK, n0);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer: tile i accumulates into TMEM buffer i % 2 once the
+        // epilogue has emptied it
         const uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % STAGES;
-            if (!umma::mbar_wait(&full_bar[s], (uint32_t)((kb / STAGES) & 1), kWaitLimit)) {
+        uint32_t it = 0, i = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+            const uint32_t buf = i & 1;
+            if (i >= 2 && !umma::mbar_wait(&tempty_bar[buf], ((i >> 1) - 1) & 1, kWaitLimit)) {
                 ok = false;
                 break;
             }
             umma::tc_fence_after();
-            const uint32_t a_addr = umma::smem_addr(smem + (size_t)s * kStageBytes);
-            const uint32_t b_addr = a_addr + kTileBytes;
+            const uint32_t acc = tmem + buf * BN;
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const uint32_t s = it % STAGES;
+                if (!umma::mbar_wait(&full_bar[s], (it / STAGES) & 1, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                umma::tc_fence_after();
+                const uint32_t a_addr = umma::smem_addr(smem + (size_t)s * kStageBytes);
+                const uint32_t b_addr = a_addr + kTileBytesA;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                // advance 16 bf16 (32 bytes) along K inside the 128-byte swizzle atom
-                umma::mma_bf16(tmem, umma::sdesc_kmajor_sw128(a_addr + kk * 32),
-                               umma::sdesc_kmajor_sw128(b_addr + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    // advance 16 bf16 (32 bytes) along K inside the 128-byte swizzle atom
+                    umma::mma_bf16(acc, umma::sdesc_kmajor_sw128(a_addr + kk * 32),
+                                   umma::sdesc_kmajor_sw128(b_addr + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                }
+                umma::mma_commit(&empty_bar[s]);
             }
-            umma::mma_commit(&empty_bar[s]);
+            umma::mma_commit(&tfull_bar[buf]);
         }
-        umma::mma_commit(&acc_bar);
-    }
-    __syncwarp();
-
-    // Epilogue: warp w owns accumulator rows 32 (w % 4) .. + 31 (TMEM lanes)
-    // and columns 64 (w / 4) .. + 63.
-    const bool acc_ok = umma::mbar_wait(&acc_bar, 0, kWaitLimit);
-    umma::tc_fence_after();
-    if (!ok || !acc_ok) {
-        if (g.err_flag) atomicExch(g.err_flag, 1);
-    } else {
-        const int quad = warp & 3, half = warp >> 2;
-        const int row = m0 + quad * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
-            uint32_t r[32];
-            umma::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-            umma::tmem_ld_wait();
-            const int nb = n0 + c0;
-            if (nb >= g.N) continue;
-            float v[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-            if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
-#pragma unroll
-                for (int c = 0; c < 32; ++c) v[c] += s_bias[c0 + c];
+    } else if (warp >= kEpiWarp0) {
+        // Epilogue: warp w owns accumulator rows 32 (w % 4) .. + 31 (TMEM
+        // lanes) and columns 128 ((w - 4) / 4) .. + 127 of each tile.
+        const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const uint32_t buf = i & 1;
+            if (!umma::mbar_wait(&tfull_bar[buf], (i >> 1) & 1, kWaitLimit)) {
+                ok = false;
+                break;
             }
-            if (MODE == EPI_GELU) {
-                if (g.out_pre) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(g.out_pre + (size_t)row * g.ld + nb);
+            umma::tc_fence_after();
+            const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+            const int row = m0 + quad * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 32) {
+                uint32_t r[32];
+                umma::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + buf * BN + (uint32_t)c0, r);
+                umma::tmem_ld_wait();
+                const int nb = n0 + c0;
+                if (nb >= g.N) continue;
+                float v[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+                if (MODE == EPI_GELU || MODE == EPI_LOGITS) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + nb);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 bb = __ldg(b4 + q);
+                        v[4 * q] += bb.x;
+                        v[4 * q + 1] += bb.y;
+                        v[4 * q + 2] += bb.z;
+                        v[4 * q + 3] += bb.w;
+                    }
+                }
+                if (MODE == EPI_GELU) {
+                    if (g.out_pre) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(g.out_pre + (size_t)row * g.ld + nb);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            __nv_bfloat162 h[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+                            dst[q] = *reinterpret_cast<uint4 *>(h);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = gelu_f(v[c]);
+                }
+                if (MODE == EPI_DGELU) {
+                    const __nv_bfloat16 *pre = g.pre_in + (size_t)row * g.ld + nb;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] *= gelu_grad_f(__bfloat162float(pre[c]));
+                }
+                if (MODE == EPI_GELU || MODE == EPI_DGELU) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld + nb);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         __nv_bfloat162 h[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+                        for (int e = 0; e < 4; ++e)
+                            h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
                         dst[q] = *reinterpret_cast<uint4 *>(h);
                     }
+                    if (g.out_bf16_t) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (nb + c < g.N) g.out_bf16_t[(size_t)(nb + c) * g.M + row] = __float2bfloat16_rn(v[c]);
+                    }
+                } else {
+                    float4 *dst = reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ld + nb);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
-#pragma unroll
-                for (int c = 0; c < 32; ++c) v[c] = gelu_f(v[c]);
             }
-            if (MODE == EPI_DGELU) {
-                const __nv_bfloat16 *pre = g.pre_in + (size_t)row * g.ld + nb;
-#pragma unroll
-                for (int c = 0; c < 32; ++c) v[c] *= gelu_grad_f(__bfloat162float(pre[c]));
-            }
-            if (MODE == EPI_GELU || MODE == EPI_DGELU) {
-                uint4 *dst = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld + nb);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    __nv_bfloat162 h[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
-                    dst[q] = *reinterpret_cast<uint4 *>(h);
-                }
-                if (g.out_bf16_t) {
-#pragma unroll
-                    for (int c = 0; c < 32; ++c)
-                        if (nb + c < g.N) g.out_bf16_t[(size_t)(nb + c) * g.M + row] = __float2bfloat16_rn(v[c]);
-                }
-            } else {
-                float4 *dst = reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ld + nb);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
+            // this warp is done with the buffer
+            umma::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tempty_bar[buf]);
         }
     }
+    if (!ok && g.err_flag) atomicExch(g.err_flag, 1);
     umma::tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 2) {
         umma::tc_fence_after();
         umma::tmem_dealloc(tmem, kTmemCols);
     }
@@ -389,14 +427,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Tensor map of a row-major BF16 matrix [rows][cols] with 128 x 64 boxes and
-// 128-byte swizzle (cols * 2 must be a multiple of 16).
-bool tmap_bf16(CUtensorMap *m, const void *ptr, int rows, int cols) {
+// Tensor map of a row-major BF16 matrix [rows][cols] with box_rows x 64 boxes
+// and 128-byte swizzle (cols * 2 must be a multiple of 16).
+bool tmap_bf16(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t gstr[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, 128};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), gdim, gstr, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -408,8 +446,11 @@ cudaError_t launch_gemm_mode(const CUtensorMap &ta, const CUtensorMap &tb, const
     auto k = gemm_bf16_kernel<MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.N + BN - 1) / BN, g.M / BM);
-    k<<<grid, kGemmThreads, kGemmSmem, s>>>(ta, tb, g);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int tiles = (g.M / BM) * ((g.N + BN - 1) / BN);
+    k<<<tiles < sms ? tiles : sms, kGemmThreads, kGemmSmem, s>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -418,7 +459,7 @@ spl_status_t gemm(int mode, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int 
                   GemmArgs g, cudaStream_t s) {
     if (M % BM || K % BK) return SPL_EINVAL;
     CUtensorMap ta, tb;
-    if (!tmap_bf16(&ta, A, M, K) || !tmap_bf16(&tb, B, Nrows_b, K)) return mfail(cudaErrorInvalidValue, "tmap");
+    if (!tmap_bf16(&ta, A, M, K, BM) || !tmap_bf16(&tb, B, Nrows_b, K, BN)) return mfail(cudaErrorInvalidValue, "tmap");
     g.M = M;
     g.N = N;
     g.K = K;
