@@ -448,7 +448,8 @@ class MLP:
 
     def batch_stationary(self, px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, out=None, offsets=None,
                          reports: bool = True, c_pixels=None, pass_kind: int = SPL_PASS_DENSE,
-                         flux_kind: int = SPL_FLUX_POINT):
+                         flux_kind: int = SPL_FLUX_POINT, threads: int = 0, tune: int = 0, state_level: int = -1,
+                         time_kernel: bool = True):
         import torch
         n = len(px)
         off = offsets_of(px)
@@ -458,7 +459,8 @@ class MLP:
             out = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
-        opts = spl_batch_opts_t(0, 0, 1, 0, 1, int(pass_kind), int(flux_kind), 0, -1)
+        opts = spl_batch_opts_t(0, 0, 1, int(threads), int(bool(time_kernel)), int(pass_kind), int(flux_kind),
+                                int(tune), int(state_level))
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
                                                 _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))
