@@ -313,6 +313,20 @@ SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_
                                                   spl_report_t *h_reports, void *stream,
                                                   const spl_batch_opts_t *opts /* nullable; warm fields ignored */);
 
+/* Self-test of the device-side bounded waits, for tests: an mbarrier phase
+ * that nothing completes (the wait gives up after a short limit), and a grid
+ * barrier of a three-CTA cooperative launch that one CTA never reaches (the
+ * polling CTA gives up, sets the error flag and writes the abort generation,
+ * and the other waiting CTA leaves on it).  No fault, trap or hang is
+ * involved.  SPL_OK if every wait gave up as designed, SPL_EINVAL if one did
+ * not, SPL_ECUDA on a CUDA error.
+ *
+ * Fault injection for tests (host side, nothing reaches the GPU): with the
+ * environment variable SPL_FAULT=alloc every batch call fails as if its first
+ * device allocation had failed (SPL_ENOMEM); with SPL_FAULT=launch as if its
+ * kernel launch had failed (SPL_ECUDA). */
+SPL_API spl_status_t spl_selftest_bounded_waits(void *stream);
+
 /* The MLP's tensor-core GEMM on its own, for tests: D[M][N] = A[M][K] B[N][K]^T
  * with row-major BF16 device matrices A, B and an FP32 device output D.
  * M % 128 == 0, K % 64 == 0, N % 32 == 0. */

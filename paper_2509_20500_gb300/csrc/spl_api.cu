@@ -816,6 +816,18 @@ spl_status_t batch_cfg(int threads, int level, int npad, bool structured, Launch
     return SPL_OK;
 }
 
+// Host-side fault injection for tests (SPL_FAULT in the environment, read at
+// every batch call): "alloc" makes the call's first device allocation fail
+// (SPL_ENOMEM), "launch" makes its kernel launch report a launch failure
+// (SPL_ECUDA).  Nothing reaches the GPU in either case.
+int injected_fault() {
+    const char *f = std::getenv("SPL_FAULT");
+    if (!f) return 0;
+    if (!std::strcmp(f, "alloc")) return 1;
+    if (!std::strcmp(f, "launch")) return 2;
+    return 0;
+}
+
 using TuneKey = std::array<int, 3>;      // padded N, structured, SMs
 using TuneVal = std::array<int, 3>;      // threads, state level, blocks per SM
 std::mutex g_tune_mu;
@@ -916,6 +928,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                        int tune = 0, int level_req = -1) {
     const int npad = batch_pad_len(nmax);
     const bool st_kind = structured != 0;
+    const int fault = injected_fault();
+    if (fault == 1) return status_of_alloc(cudaErrorMemoryAllocation, "px (injected)");
     cudaError_t e;
     if ((e = grow(&ws.px, &ws.px_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "px");
     if ((e = grow(&ws.reps, &ws.reps_cap, (size_t)n)) != cudaSuccess) return status_of_alloc(e, "reports");
@@ -969,6 +983,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
             }
         }
     }
+    if (fault == 2) return note_cuda_error(cudaErrorLaunchFailure, "batch launch (injected)");
     if (time_kernel) {
         if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
@@ -1133,6 +1148,26 @@ extern "C" spl_status_t spl_batch_kernel_ms(float *ms) {
     SPL_CU(cudaEventSynchronize(ws->ev1));
     SPL_CU(cudaEventElapsedTime(ms, ws->ev0, ws->ev1));
     return SPL_OK;
+}
+
+extern "C" spl_status_t spl_selftest_bounded_waits(void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned *bar = nullptr;
+    int *flags = nullptr;   // [0] error flag, [1] mbarrier wait gave up, [2] CTAs that saw the abort
+    cudaError_t e = cudaMalloc(&bar, sizeof(unsigned) * chain_run_bar_words());
+    if (e == cudaSuccess) e = cudaMalloc(&flags, 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(unsigned) * chain_run_bar_words(), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), s);
+    if (e == cudaSuccess) e = launch_selftest_waits(bar, flags, flags + 1, s);
+    int h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (bar) cudaFree(bar);
+    if (flags) cudaFree(flags);
+    if (e != cudaSuccess) return note_cuda_error(e, "bounded-wait self-test");
+    // the mbarrier wait gave up; the polling CTA gave up and set the error
+    // flag; both CTAs that reached the grid barrier left it on the abort
+    return (h[0] == 1 && h[1] == 1 && h[2] == 2) ? SPL_OK : SPL_EINVAL;
 }
 
 // ======================================================================

@@ -1007,9 +1007,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 
 // Bounded wait on an mbarrier phase; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
     const uint32_t addr = smem_u32(bar);
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1255,7 +1255,8 @@ __device__ __forceinline__ int add_acq_rel_gpu(int *p, int v) {
 // launch, bar[kBarGen] (another 128-byte line) is the released generation;
 // gen is the calling CTA's count of barriers passed (thread 0's copy is the
 // one used).  False if the grid was aborted.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag) {
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag,
+                                          uint32_t limit = kGridSpinLimit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
@@ -1265,7 +1266,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err
             const unsigned target = next * gridDim.x;
             uint32_t spins = 0;
             while ((int)(ld_acquire_gpu(&bar[0]) - target) < 0) {
-                if (++spins > kGridSpinLimit) {
+                if (++spins > limit) {
                     ok = false;
                     break;
                 }
@@ -1280,7 +1281,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err
             unsigned g;
             uint32_t spins = 0;
             while ((g = ld_acquire_gpu(&bar[kBarGen])) == gen) {
-                if (++spins > kGridSpinLimit) {
+                if (++spins > limit) {
                     atomicExch(err_flag, 1);
                     atomicExch(&bar[kBarGen], kBarAbort);
                     g = kBarAbort;
@@ -1553,6 +1554,43 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
                 make_float4(stats[0], stats[1], stats[2], stats[3]);
         vsrc = vdst;
     }
+}
+
+// ======================================================================
+// Self-test of the bounded waits
+// ======================================================================
+//
+// The waits of the kernels above give up after a limit and report; these two
+// kernels make such waits run out on purpose, with short limits: an mbarrier
+// phase that nothing completes, and a grid barrier that one CTA of a
+// cooperative launch never reaches (the polling CTA gives up and writes the
+// abort generation, which releases the other waiting CTA).
+
+__global__ void selftest_mbar_kernel(int *status, uint32_t limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        status[0] = mbar_wait(&bar, 0, limit) ? 0 : 1;   // nothing arrives
+    }
+}
+
+__global__ void selftest_grid_kernel(unsigned *bar, int *err_flag, int *status, uint32_t limit) {
+    __shared__ int s_flag;
+    unsigned gen = 0u;
+    if (blockIdx.x == gridDim.x - 1) return;             // this CTA never arrives
+    const bool ok = grid_sync(bar, gen, err_flag, &s_flag, limit);
+    if (threadIdx.x == 0 && !ok) atomicAdd(status + 1, 1);
+}
+
+cudaError_t launch_selftest_waits(unsigned *bar, int *err_flag, int *status, cudaStream_t s) {
+    selftest_mbar_kernel<<<1, 32, 0, s>>>(status, 1u << 14);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t limit = 1u << 16;
+    void *params[] = {&bar, &err_flag, &status, &limit};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(selftest_grid_kernel), dim3(3), dim3(32), params,
+                                       0, s);
 }
 
 // ======================================================================

@@ -104,6 +104,10 @@ size_t chain_run_smem_bytes(int chunk);
 // CTAs per SM the cooperative launch can keep resident (0 on error).
 int chain_run_blocks_per_sm(int chunk);
 cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s);
+// Waits that run out on purpose (status[0]: the mbarrier wait gave up;
+// status[1]: CTAs that left the grid barrier on the abort; err_flag set by the
+// CTA that gave up).  bar: chain_run_bar_words() zeroed words.
+cudaError_t launch_selftest_waits(unsigned *bar, int *err_flag, int *status, cudaStream_t s);
 
 struct FinishArgs {
     int mode;                // 0 materialised (GEMV partials), 1 fused (split partials)

@@ -234,6 +234,51 @@ def test_tune_cache_file_is_read(tmp_path):
     np.testing.assert_array_equal(np.load(tmp_path / "a.npy"), np.load(tmp_path / "b.npy"))
 
 
+def test_bounded_waits_give_up_and_context_stays_usable(spl):
+    """The device-side waits give up after their limit: an mbarrier phase
+    nothing completes and a grid barrier one CTA never reaches end with the
+    designed status (no fault, trap or hang), and the context still runs a
+    batch correctly afterwards."""
+    assert spl.selftest_bounded_waits() == spl.SPL_OK
+    px = W.random_small(4, seed=91, n_min=50, n_max=300)
+    out, off, reps = spl.batch_stationary(px, tol=1e-6)
+    assert np.all(reps["status"] == 0)
+    o = out.cpu().numpy()
+    for k, p in enumerate(W.as_dicts(px)):
+        ref = oracle.stationary(p, shift=oracle.shift_l(p))
+        assert _l1(o[off[k]:off[k + 1]], ref) < L1_TOL
+
+
+@pytest.mark.parametrize("kind,status", [("alloc", "SPL_ENOMEM"), ("launch", "SPL_ECUDA")])
+def test_injected_host_faults_give_clean_status(kind, status, tmp_path):
+    """SPL_FAULT=alloc|launch: a batch call fails with the matching status
+    before anything reaches the GPU, and once the variable is gone the same
+    process runs the batch."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import os, sys, numpy as np\n"
+        "from paper_2509_20500_gb300 import spl, workloads as W\n"
+        "px = W.random_small(3, seed=92, n_min=40, n_max=200)\n"
+        "try:\n"
+        "    spl.batch_stationary(px)\n"
+        "    print('no error')\n"
+        "except spl.SplError as e:\n"
+        "    print('status', e.status)\n"
+        "os.environ.pop('SPL_FAULT')\n"
+        "out, off, reps = spl.batch_stationary(px)\n"
+        "print('after', int(np.all(reps['status'] == 0)))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPL_FAULT=kind, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.strip().splitlines()
+    from paper_2509_20500_gb300 import spl as S
+    assert lines[-2] == "status %d" % getattr(S, status), lines
+    assert lines[-1] == "after 1"
+
+
 def test_pure_background_uniform(spl):
     px = W.pixel(999, 33.3, 30.0, 0.5, 0.0, 2.0)
     for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
