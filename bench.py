@@ -555,7 +555,9 @@ def run_gpu(args):
     h2d = n * 56
     d2h = total * 4
 
-    launches = 1 + (6 if learned else 0)
+    # per step: pixel_const_kernel + batch_fused_kernel, and for the learned
+    # start features_kernel + five GEMMs
+    launches = 2 + (6 if learned else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -295,6 +295,12 @@ SPL_API spl_status_t spl_mlp_create(int32_t max_batch, uint64_t seed, void *stre
 SPL_API int64_t spl_mlp_param_count(void);
 SPL_API spl_status_t spl_mlp_set_params(spl_mlp_t *m, const float *h_params, int64_t count);
 SPL_API spl_status_t spl_mlp_get_params(spl_mlp_t *m, float *h_params, int64_t count);
+/* AdamW state for checkpoints: h_state holds 2 x spl_mlp_param_count()
+ * floats, the first moments then the second moments, each packed like the
+ * parameters; *step / step is the optimiser step count (bias correction).
+ * With the parameters it resumes training exactly. */
+SPL_API spl_status_t spl_mlp_get_state(spl_mlp_t *m, float *h_state, int64_t count, int32_t *step);
+SPL_API spl_status_t spl_mlp_set_state(spl_mlp_t *m, const float *h_state, int64_t count, int32_t step);
 SPL_API spl_status_t spl_mlp_forward(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, float *d_logits);
 /* Device time of the forward pass alone: uploads the pixels once, then times
  * `reps` forward passes (features and the five GEMMs, logits kept inside the

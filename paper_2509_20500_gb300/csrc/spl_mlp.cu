@@ -757,6 +757,41 @@ extern "C" spl_status_t spl_mlp_get_params(spl_mlp_t *m, float *h, int64_t count
     return get_packed(m, m->W, m->b, h);
 }
 
+static spl_status_t set_packed(spl_mlp_t *m, float *const *W, float *const *b, const float *h) {
+    MCU(cudaStreamSynchronize(m->stream));
+    const float *p = h;
+    for (int l = 0; l < kLayers; ++l) {
+        std::vector<float> w((size_t)kRows[l] * kCols[l], 0.f), bb(kRows[l], 0.f);
+        for (int r = 0; r < kNreal[l]; ++r)
+            for (int k = 0; k < kKreal[l]; ++k) w[(size_t)r * kCols[l] + k] = *p++;
+        for (int r = 0; r < kNreal[l]; ++r) bb[r] = *p++;
+        MCU(cudaMemcpy(W[l], w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+        MCU(cudaMemcpy(b[l], bb.data(), sizeof(float) * bb.size(), cudaMemcpyHostToDevice));
+    }
+    return SPL_OK;
+}
+
+// AdamW state: first moments then second moments, each packed like the
+// parameters (padding entries stay zero: their gradients are zero), and the
+// step count used for bias correction.
+extern "C" spl_status_t spl_mlp_get_state(spl_mlp_t *m, float *h, int64_t count, int32_t *step) {
+    const int64_t pc = packed_count();
+    if (!m || !h || !step || count != 2 * pc) return SPL_EINVAL;
+    spl_status_t st = get_packed(m, m->mW, m->mb, h);
+    if (st == SPL_OK) st = get_packed(m, m->vW, m->vb, h + pc);
+    if (st == SPL_OK) *step = m->step;
+    return st;
+}
+
+extern "C" spl_status_t spl_mlp_set_state(spl_mlp_t *m, const float *h, int64_t count, int32_t step) {
+    const int64_t pc = packed_count();
+    if (!m || !h || count != 2 * pc || step < 0) return SPL_EINVAL;
+    spl_status_t st = set_packed(m, m->mW, m->mb, h);
+    if (st == SPL_OK) st = set_packed(m, m->vW, m->vb, h + pc);
+    if (st == SPL_OK) m->step = step;
+    return st;
+}
+
 extern "C" spl_status_t spl_mlp_forward(spl_mlp_t *m, const spl_pixel_t *h_px, int32_t n, float *d_logits) {
     spl_status_t st = check_batch(m, h_px, n);
     if (st != SPL_OK) return st;

@@ -54,7 +54,7 @@ REPORT_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("last_step_
 EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_stationary_ex", "spl_batch_kernel_ms",
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
-            "spl_mlp_get_params", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
+            "spl_mlp_get_params", "spl_mlp_get_state", "spl_mlp_set_state", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
 
@@ -122,6 +122,10 @@ def lib():
         L.spl_mlp_set_params.restype = ctypes.c_int
         L.spl_mlp_get_params.argtypes = [vp, vp, ctypes.c_int64]
         L.spl_mlp_get_params.restype = ctypes.c_int
+        L.spl_mlp_get_state.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
+        L.spl_mlp_get_state.restype = ctypes.c_int
+        L.spl_mlp_set_state.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32]
+        L.spl_mlp_set_state.restype = ctypes.c_int
         L.spl_mlp_forward.argtypes = [vp, P, i32, vp]
         L.spl_mlp_forward.restype = ctypes.c_int
         L.spl_mlp_time_forward.argtypes = [vp, P, i32, i32, fp]
@@ -425,6 +429,19 @@ class MLP:
     def set_params(self, p: np.ndarray):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(lib().spl_mlp_set_params(self._m, ctypes.c_void_p(p.ctypes.data), p.size), "spl_mlp_set_params")
+
+    def get_state(self):
+        """AdamW state (moments packed like the parameters) and step count."""
+        out = np.empty(2 * self.param_count(), dtype=np.float32)
+        step = ctypes.c_int32()
+        _check(lib().spl_mlp_get_state(self._m, ctypes.c_void_p(out.ctypes.data), out.size, ctypes.byref(step)),
+               "spl_mlp_get_state")
+        return out, int(step.value)
+
+    def set_state(self, state: np.ndarray, step: int):
+        state = np.ascontiguousarray(state, dtype=np.float32)
+        _check(lib().spl_mlp_set_state(self._m, ctypes.c_void_p(state.ctypes.data), state.size, int(step)),
+               "spl_mlp_set_state")
 
     def time_forward(self, px: np.ndarray, reps: int = 10) -> float:
         """Device ms of one forward pass (kernels only) over px."""

@@ -62,11 +62,16 @@ def train(px, targets, epochs: int = 20, batch: int = 4096, lr: float = 2e-3, wa
 
 
 def save(net, path: str, seed: int = 0, steps: int = 0):
-    np.savez(path, params=net.get_params(), seed=seed, steps=steps)
+    """Checkpoint: FP32 parameters, the AdamW moments and step count (so
+    training resumes exactly), the seed and the caller's step count."""
+    state, opt_step = net.get_state()
+    np.savez(path, params=net.get_params(), adam=state, adam_step=opt_step, seed=seed, steps=steps)
 
 
 def load(path: str, max_batch: int = 4096):
     d = np.load(path)
     net = spl.MLP(max_batch=max_batch, seed=int(d["seed"]))
     net.set_params(d["params"])
+    if "adam" in d:
+        net.set_state(d["adam"], int(d["adam_step"]))
     return net

@@ -178,3 +178,38 @@ def test_headline_launch_array256_learned_sampled(spl):
     worst = max(np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() for r, k in enumerate(idx))
     assert worst < 1e-6, worst
     net.close()
+
+
+def test_checkpoint_resumes_training_exactly(spl, tmp_path):
+    """train.save / train.load keep the parameters, the AdamW moments and the
+    step count: 3 steps, a checkpoint, a new network loaded from it and 3 more
+    steps give the same parameters bit for bit as 6 steps without a break."""
+    from paper_2509_20500_gb300 import train as T
+    data = W.training(2048, seed=4)
+    tgt, _, _ = spl.batch_stationary(data, tol=1e-6)
+    tgt = tgt.view(len(data), 2000)
+    c = [spl.pixels_to_c(data[i:i + 1024]) for i in (0, 1024)]
+    lrs = [1e-3, 2e-3, 3e-3, 3e-3, 2e-3, 1e-3]
+
+    def step(net, k):
+        b = k % 2
+        net.train_step(c[b], 1024, tgt[b * 1024:(b + 1) * 1024], lr=lrs[k], weight_decay=1e-4)
+
+    a = spl.MLP(max_batch=1024, seed=7)
+    for k in range(6):
+        step(a, k)
+    b = spl.MLP(max_batch=1024, seed=7)
+    for k in range(3):
+        step(b, k)
+    T.save(b, str(tmp_path / "ck.npz"), seed=7, steps=3)
+    b.close()
+    r = T.load(str(tmp_path / "ck.npz"), max_batch=1024)
+    for k in range(3, 6):
+        step(r, k)
+    np.testing.assert_array_equal(r.get_params(), a.get_params())
+    sa, na = a.get_state()
+    sr, nr = r.get_state()
+    assert na == nr == 6
+    np.testing.assert_array_equal(sr, sa)
+    a.close()
+    r.close()
