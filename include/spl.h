@@ -319,6 +319,18 @@ SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_
                                                   spl_report_t *h_reports, void *stream,
                                                   const spl_batch_opts_t *opts /* nullable; warm fields ignored */);
 
+/* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
+ * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a
+ * chain of n_bins bins runs on `grid` CTAs; its column pass is cut into
+ * tiles x row_blocks equal units (128 columns x 32 rows, vlen = rows padded),
+ * CTA b taking units [b U / grid, (b+1) U / grid) with U = tiles x
+ * row_blocks; `segs` partial slots per CTA; at most `chunk` rows staged in
+ * shared memory at once.  SPL_EINVAL on bad arguments. */
+typedef struct {
+    int32_t grid, tiles, row_blocks, segs, chunk, vlen;
+} spl_run_plan_t;
+SPL_API spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t blocks_per_sm, spl_run_plan_t *out);
+
 /* Self-test of the device-side bounded waits, for tests: an mbarrier phase
  * that nothing completes (the wait gives up after a short limit), and a grid
  * barrier of a three-CTA cooperative launch that one CTA never reaches (the

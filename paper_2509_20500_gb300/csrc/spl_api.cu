@@ -213,18 +213,17 @@ static void plan_split(spl_chain *c) {
     c->ld_part = c->vlen;
 }
 
-// Plan of the persistent fused iteration: as many CTAs as stay resident (at
-// most one per work unit), the work units (128-column tile x 32-row block)
-// split evenly over them, and the partial slots one CTA needs.
-static spl_status_t plan_run(spl_chain *c) {
-    const int sms = num_sms_current();
-    const int maxc = chain_run_max_chunk();
-    const int bps = std::min(2, chain_run_blocks_per_sm(maxc));
-    if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "chain run occupancy");
-    const int T = (c->N + chain_run_tile_cols() - 1) / chain_run_tile_cols();
-    const int RB = c->vlen / 32;
+// Plan of the persistent fused iteration (host arithmetic only): as many CTAs
+// as stay resident (at most one per work unit), the work units (128-column
+// tile x 32-row block) split evenly over them, the partial slots one CTA
+// needs and the rows it stages at once.
+extern "C" spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t blocks_per_sm, spl_run_plan_t *out) {
+    if (!out || n_bins < 2 || n_bins > kMaxBins || sms < 1 || blocks_per_sm < 1) return SPL_EINVAL;
+    const int vlen = split_pad_len(n_bins);
+    const int T = (n_bins + chain_run_tile_cols() - 1) / chain_run_tile_cols();
+    const int RB = vlen / 32;
     const long long U = (long long)T * RB;
-    const int G = (int)std::min<long long>(std::min(bps * sms, chain_run_max_grid()), U);
+    const int G = (int)std::min<long long>(std::min((long long)blocks_per_sm * sms, (long long)chain_run_max_grid()), U);
     int segs = 1;
     long long umax = 0;
     for (int b = 0; b < G; ++b) {
@@ -232,17 +231,33 @@ static spl_status_t plan_run(spl_chain *c) {
         segs = std::max(segs, (int)((u1 - 1) / RB - u0 / RB) + 1);
         umax = std::max(umax, u1 - u0);
     }
+    out->grid = G;
+    out->tiles = T;
+    out->row_blocks = RB;
+    out->segs = segs;
+    out->chunk = (int)std::min<long long>(chain_run_max_chunk(), umax * 32);
+    out->vlen = vlen;
+    return SPL_OK;
+}
+
+static spl_status_t plan_run(spl_chain *c) {
+    const int bps = std::min(2, chain_run_blocks_per_sm(chain_run_max_chunk()));
+    if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "chain run occupancy");
+    spl_run_plan_t pl;
+    spl_status_t st = spl_chain_run_plan(c->N, num_sms_current(), bps, &pl);
+    if (st != SPL_OK) return st;
+    const int T = pl.tiles, G = pl.grid;
     c->run_T = T;
-    c->run_RB = RB;
-    c->run_segs = segs;
-    c->run_chunk = (int)std::min<long long>(maxc, umax * 32);
+    c->run_RB = pl.row_blocks;
+    c->run_segs = pl.segs;
+    c->run_chunk = pl.chunk;
     c->run_grid = G;
     SPL_CU(dalloc(&c->run_y, 2 * (size_t)c->vlen));
     SPL_CU(dalloc(&c->run_vb, 2 * (size_t)c->vlen));
     SPL_CU(cudaMemset(c->run_vb, 0, 2 * sizeof(float) * c->vlen));
     SPL_CU(dalloc(&c->run_pi, (size_t)c->N));
     SPL_CU(dalloc(&c->run_tsum, 2 * (size_t)T));
-    SPL_CU(dalloc(&c->run_part, (size_t)G * segs * chain_run_tile_cols()));
+    SPL_CU(dalloc(&c->run_part, (size_t)G * pl.segs * chain_run_tile_cols()));
     SPL_CU(dalloc(&c->run_blk, 2 * (size_t)G * 4));
     SPL_CU(dalloc(&c->run_ticket, (size_t)T));
     SPL_CU(dalloc(&c->run_bar, (size_t)chain_run_bar_words()));

@@ -55,7 +55,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_get_state", "spl_mlp_set_state", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
-            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits",
+            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
 
 _lib = None
@@ -157,6 +157,8 @@ def lib():
         L.spl_chain_time_step.restype = ctypes.c_int
         L.spl_selftest_bounded_waits.argtypes = [vp]
         L.spl_selftest_bounded_waits.restype = ctypes.c_int
+        L.spl_chain_run_plan.argtypes = [i32, i32, i32, ctypes.POINTER(spl_run_plan_t)]
+        L.spl_chain_run_plan.restype = ctypes.c_int
         L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         L.spl_gemm_bf16.restype = ctypes.c_int
         _lib = L
@@ -363,6 +365,19 @@ def batch_spectral(px: np.ndarray, subspace_iters: int = 60, stream=None):
     _check(lib().spl_batch_spectral(pixels_to_c(px), len(px), int(subspace_iters), _dptr(out), _stream_ptr(stream)),
            "spl_batch_spectral")
     return out[:len(px)]
+
+
+class spl_run_plan_t(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("tiles", ctypes.c_int32), ("row_blocks", ctypes.c_int32),
+                ("segs", ctypes.c_int32), ("chunk", ctypes.c_int32), ("vlen", ctypes.c_int32)]
+
+
+def chain_run_plan(n_bins: int, sms: int, blocks_per_sm: int) -> dict:
+    """spl_chain_run_plan (host arithmetic, no GPU needed)."""
+    pl = spl_run_plan_t()
+    _check(lib().spl_chain_run_plan(int(n_bins), int(sms), int(blocks_per_sm), ctypes.byref(pl)),
+           "spl_chain_run_plan")
+    return {k: int(getattr(pl, k)) for k, _ in spl_run_plan_t._fields_}
 
 
 def selftest_bounded_waits(stream=None) -> int:

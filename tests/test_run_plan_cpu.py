@@ -1,0 +1,70 @@
+"""Work partition of the fused chain's persistent iteration (host arithmetic,
+no GPU): every (128-column tile, 32-row block) unit has exactly one CTA, the
+owner formula the kernel uses finds it, a CTA shares at most its first and
+last tile with other CTAs, its partial slots fit `segs`, and the rows it
+stages at once fit `chunk`."""
+import numpy as np
+import pytest
+
+from paper_2509_20500_gb300 import spl
+
+
+def _owner(u, U, G):
+    # the kernel's inverse of u0(b) = floor(b U / G)
+    return ((u + 1) * G + U - 1) // U - 1
+
+
+def _check(n, sms, bps):
+    pl = spl.chain_run_plan(n, sms, bps)
+    G, T, RB, segs, chunk, vlen = (pl[k] for k in ("grid", "tiles", "row_blocks", "segs", "chunk", "vlen"))
+    assert vlen >= n and vlen % 128 == 0 and RB == vlen // 32
+    assert T == (n + 127) // 128
+    U = T * RB
+    assert 1 <= G <= min(bps * sms, 512, U)
+    start = [b * U // G for b in range(G + 1)]
+    assert start[0] == 0 and start[-1] == U
+    assert all(start[b + 1] > start[b] for b in range(G))      # no CTA without work
+    umax = max(start[b + 1] - start[b] for b in range(G))
+    assert chunk == min(8192, 32 * umax)
+    # owner formula against the actual ranges (sampled units for large U)
+    rng = np.random.default_rng(n + sms)
+    us = set(rng.integers(0, U, size=min(U, 4000)).tolist()) | {0, U - 1} | set(start[1:-1])
+    bs = np.searchsorted(np.asarray(start), np.asarray(sorted(us)), side="right") - 1
+    for u, b in zip(sorted(us), bs):
+        assert _owner(u, U, G) == b, (n, u)
+    shared = {}
+    for b in range(G):
+        u0, u1 = start[b], start[b + 1]
+        tf, tl = u0 // RB, (u1 - 1) // RB
+        assert tl - tf + 1 <= segs
+        own_first = u0 == tf * RB and u1 >= (tf + 1) * RB
+        own_last = u1 == (tl + 1) * RB and u0 <= tl * RB
+        for t in (tf, tl):
+            if not (own_first if t == tf else own_last):
+                shared.setdefault(t, set()).add(b)
+    # a shared tile's contributors are the CTAs owner(first unit) .. owner(last unit)
+    for t, cs in shared.items():
+        bf, bl = _owner(t * RB, U, G), _owner((t + 1) * RB - 1, U, G)
+        assert cs == set(range(bf, bl + 1)) and len(cs) >= 2, (n, t)
+    return pl
+
+
+@pytest.mark.parametrize("n", [2, 3, 100, 127, 128, 129, 1000, 1500, 2000, 3000, 4100, 9000, 10000, 16000,
+                               18000, 50000, 200000])
+def test_partition_invariants(n):
+    for sms, bps in ((152, 2), (148, 2), (152, 1), (7, 2), (1, 1)):
+        _check(n, sms, bps)
+
+
+def test_partition_sizes_used_by_the_gpu_tests():
+    # N = 10000: two tiles per CTA at most; N = 18000: more rows than one window
+    p = _check(10000, 152, 2)
+    assert (p["grid"], p["tiles"], p["segs"], p["chunk"]) == (304, 79, 2, 2656)
+    p = _check(18000, 152, 2)
+    assert p["chunk"] == 8192 and p["segs"] == 2
+
+
+def test_plan_rejects_bad_arguments():
+    for args in ((1, 152, 2), (2000, 0, 2), (2000, 152, 0), ((1 << 24) + 1, 152, 2)):
+        with pytest.raises(spl.SplError):
+            spl.chain_run_plan(*args)
