@@ -273,8 +273,9 @@ SPL_API spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels, i
  * accumulation on the tensor cores, maps (sub-bin pulse position, sigma,
  * log S, log B, x_d / t_r) of an n_bins = 2000 pixel to a log-correction of
  * the flux prior lambda(s_j) in a frame rolled to the pulse bin; its softmax
- * starts the power iteration, which always runs to the stop rule (the plain
- * iteration is the judge of the network's error).
+ * starts the power iteration, which always runs to the stop rule (so the
+ * network changes how many steps are needed, never the accuracy of the
+ * result).
  *   spl_mlp_create   : device network for batches of up to max_batch pixels,
  *                      seeded uniform fan-in initialisation; owns its scratch.
  *   spl_mlp_param_count / set_params / get_params : packed FP32 parameters,
