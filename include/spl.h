@@ -233,7 +233,10 @@ SPL_API spl_status_t spl_batch_kernel_ms(float *ms);
  * Same computation as spl_batch_stationary with HOST buffers: h_warm (NULL or
  * packed host floats), h_out (packed host floats, offsets from the n_bins of
  * h_pixels in order) and h_reports (may be NULL).  Copies inputs to the device
- * and results back inside the call; synchronises `stream`.
+ * and results back inside the call; synchronises `stream`.  A batch of one
+ * size runs as four consecutive ranges of at least four waves each, and each
+ * range's results are copied back on a library-owned stream while the next
+ * range computes (same pmfs bit for bit as one launch).
  */
 SPL_API spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
                                        const float *h_warm, float *h_out, spl_report_t *h_reports,
@@ -319,6 +322,14 @@ SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_
                                                   int32_t max_iter, float *d_out, const int64_t *d_offsets,
                                                   spl_report_t *h_reports, void *stream,
                                                   const spl_batch_opts_t *opts /* nullable; warm fields ignored */);
+/* The same from and to host memory: pmfs into h_out (packed in caller order,
+ * sum of n_bins floats; pinned memory copies fastest).  A batch of one size
+ * runs as four consecutive ranges whose device-to-host copies overlap the next
+ * range's compute (same pmfs bit for bit). */
+SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n,
+                                                       double tol, int32_t max_iter, float *h_out,
+                                                       spl_report_t *h_reports, void *stream,
+                                                       const spl_batch_opts_t *opts /* nullable */);
 
 /* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
  * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <functional>
 #include <map>
 #include <array>
 #include <cmath>
@@ -720,6 +721,9 @@ struct BatchWorkspace {
     std::vector<int64_t> offs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
+    // copies of the host-buffer entry points overlap the next range's compute
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_range = nullptr;
 };
 
 constexpr int kMaxDevices = 64;
@@ -882,9 +886,9 @@ bool tune_lookup(const TuneKey &k, TuneVal *v) {
     return true;
 }
 
-// One launch of the batch kernel over the first n items of the uploaded work
-// list with configuration cfg (a holds everything else).
-spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, int32_t n, int npad,
+// One launch of the batch kernel over items [start, start + n) of the
+// uploaded work list with configuration cfg (a holds everything else).
+spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, int32_t start, int32_t n, int npad,
                         cudaStream_t s) {
     int grid = cfg.bps * num_sms_current();
     if (grid > n) grid = n;
@@ -893,6 +897,8 @@ spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, i
     if (per_block && (e = grow(&ws.scratch, &ws.scratch_cap, (size_t)grid * per_block)) != cudaSuccess)
         return status_of_alloc(e, "scratch");
     SPL_CU(cudaMemsetAsync(ws.counter, 0, sizeof(int), s));
+    a.px = ws.px + start;
+    a.pconst = ws.pconst + start;
     a.n = n;
     a.scratch = ws.scratch;
     a.state_level = cfg.level;
@@ -916,10 +922,10 @@ spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int n
             LaunchCfg cfg = top;
             cfg.bps = bps;
             // untimed: loads the kernel's module and settles the clocks
-            spl_status_t st = launch_cfg(ws, a, cfg, std::min<int32_t>(sample, cfg.bps * sms), npad, s);
+            spl_status_t st = launch_cfg(ws, a, cfg, 0, std::min<int32_t>(sample, cfg.bps * sms), npad, s);
             if (st != SPL_OK) return st;
             SPL_CU(cudaEventRecord(ws.ev0, s));
-            if ((st = launch_cfg(ws, a, cfg, sample, npad, s)) != SPL_OK) return st;
+            if ((st = launch_cfg(ws, a, cfg, 0, sample, npad, s)) != SPL_OK) return st;
             SPL_CU(cudaEventRecord(ws.ev1, s));
             SPL_CU(cudaEventSynchronize(ws.ev1));
             float ms = 0.f;
@@ -935,12 +941,15 @@ spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int n
 
 // Launches the persistent batch kernel; out/warm are packed by caller order.
 // tune: 0 measured configuration (cached), 1 the fixed heuristic, 2 the
-// caller's threads and state level.
+// caller's threads and state level.  chunks > 1 splits the work list into
+// that many consecutive ranges (each still filling the GPU), one launch each,
+// with after_range(start, count) called once a range is enqueued.
+using RangeFn = std::function<spl_status_t(int32_t, int32_t)>;
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
                        cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0,
-                       int tune = 0, int level_req = -1) {
+                       int tune = 0, int level_req = -1, int chunks = 1, const RangeFn *after_range = nullptr) {
     const int npad = batch_pad_len(nmax);
     const bool st_kind = structured != 0;
     const int fault = injected_fault();
@@ -1004,7 +1013,13 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
         SPL_CU(cudaEventRecord(ws.ev0, s));
     }
-    if ((st = launch_cfg(ws, a, cfg, n, npad, s)) != SPL_OK) return st;
+    const int per_wave = std::max(1, cfg.bps * num_sms_current());
+    const int K = std::max(1, std::min(chunks, n / (4 * per_wave)));
+    for (int c = 0; c < K; ++c) {
+        const int32_t lo = (int32_t)((int64_t)n * c / K), hi = (int32_t)((int64_t)n * (c + 1) / K);
+        if ((st = launch_cfg(ws, a, cfg, lo, hi - lo, npad, s)) != SPL_OK) return st;
+        if (after_range && (st = (*after_range)(lo, hi - lo)) != SPL_OK) return st;
+    }
     if (time_kernel) {
         SPL_CU(cudaEventRecord(ws.ev1, s));
         ws.timed = true;
@@ -1080,33 +1095,81 @@ extern "C" spl_status_t spl_batch_stationary(const spl_pixel_t *h_pixels, int32_
     return spl_batch_stationary_ex(h_pixels, n, tol, max_iter, d_warm, d_out, d_offsets, h_reports, stream, nullptr);
 }
 
-extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol,
-                                                  int32_t max_iter, const float *h_warm, float *h_out,
-                                                  spl_report_t *h_reports, void *stream) {
+// Host-buffer batch: pmfs into pinned or pageable h_out (packed in caller
+// order), reports into h_reports (may be NULL).  A batch of one size runs as
+// four consecutive ranges whose device-to-host copies (on a second stream)
+// overlap the next range's compute; other batches run as one launch.
+spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                                 const float *d_warm, const float *h_warm, int warm_kind, int warm_ld, float *h_out,
+                                 spl_report_t *h_reports, cudaStream_t s, const spl_batch_opts_t *opts) {
     if (n < 0 || (n > 0 && (!h_pixels || !h_out)) || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
     if (n == 0) return SPL_OK;
+    const int min_iter = opts ? opts->min_iter : 1;
+    const int threads = opts ? opts->threads : 0;
+    const int structured = opts ? opts->pass_kind : 0;
+    const int flux_kind = opts ? opts->flux_kind : 0;
+    const int tune = opts ? opts->tune : 0;
+    const int level = opts ? opts->state_level : -1;
+    if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    if (flux_kind != SPL_FLUX_POINT && flux_kind != SPL_FLUX_BININT) return SPL_EINVAL;
+    if (tune < 0 || tune > 2 || (tune == 2 && (level < 0 || level > 2))) return SPL_EINVAL;
     BatchWorkspace *ws = nullptr;
     spl_status_t st = ws_get(&ws);
     if (st != SPL_OK) return st;
     std::lock_guard<std::mutex> lock(ws->mu);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int nmax = 0;
     st = make_work_list(*ws, h_pixels, n, &nmax);
     if (st != SPL_OK) return st;
-    size_t total = 0;
-    for (int32_t k = 0; k < n; ++k) total += (size_t)h_pixels[k].n_bins;
+    if (d_warm && warm_kind == 2) {
+        for (int32_t k = 0; k < n; ++k)
+            if (warm_ld < h_pixels[k].n_bins) return SPL_EINVAL;
+    }
+    const std::vector<int64_t> &off = ws->offs;
+    const size_t total = (size_t)off[(size_t)n];
+    bool uniform = true;
+    for (int32_t k = 1; k < n && uniform; ++k) uniform = h_pixels[k].n_bins == h_pixels[0].n_bins;
     cudaError_t e;
     if ((e = grow(&ws->d_out, &ws->out_cap, total)) != cudaSuccess) return status_of_alloc(e, "out");
     if (h_warm) {
         if ((e = grow(&ws->d_warm, &ws->warm_cap, total)) != cudaSuccess) return status_of_alloc(e, "warm");
         SPL_CU(cudaMemcpyAsync(ws->d_warm, h_warm, sizeof(float) * total, cudaMemcpyHostToDevice, s));
+        d_warm = ws->d_warm;
+        warm_kind = 0;
+        warm_ld = 0;
     }
-    st = run_batch(*ws, n, nmax, tol, max_iter, h_warm ? ws->d_warm : nullptr, 0, 0, 1, 0, ws->d_out, nullptr, s);
-    if (st != SPL_OK) return st;
-    SPL_CU(cudaMemcpyAsync(h_out, ws->d_out, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    if (!ws->copy_stream) SPL_CU(cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking));
+    if (!ws->ev_range) SPL_CU(cudaEventCreateWithFlags(&ws->ev_range, cudaEventDisableTiming));
+    float *d_out = ws->d_out;
+    cudaStream_t cs = ws->copy_stream;
+    cudaEvent_t ev = ws->ev_range;
+    // in a batch of one size the work list keeps the caller's order, so a
+    // range of it is a contiguous slice of the packed output
+    const RangeFn copy_range = [&](int32_t lo, int32_t cnt) -> spl_status_t {
+        const int64_t o0 = uniform ? off[(size_t)lo] : 0, o1 = uniform ? off[(size_t)(lo + cnt)] : (int64_t)total;
+        if (!uniform && lo + cnt < n) return SPL_OK;      // one copy after the last range
+        SPL_CU(cudaEventRecord(ev, s));
+        SPL_CU(cudaStreamWaitEvent(cs, ev, 0));
+        SPL_CU(cudaMemcpyAsync(h_out + o0, d_out + o0, sizeof(float) * (size_t)(o1 - o0), cudaMemcpyDeviceToHost,
+                               cs));
+        return SPL_OK;
+    };
+    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, warm_kind, warm_ld, min_iter, threads, d_out, nullptr, s,
+                   false, structured, flux_kind, tune, tune == 2 ? level : -1, uniform ? 4 : 1, &copy_range);
+    if (st != SPL_OK) {
+        cudaStreamSynchronize(cs);
+        return st;
+    }
+    SPL_CU(cudaStreamSynchronize(cs));
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     SPL_CU(cudaStreamSynchronize(s));
     return SPL_OK;
+}
+
+extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol,
+                                                  int32_t max_iter, const float *h_warm, float *h_out,
+                                                  spl_report_t *h_reports, void *stream) {
+    return batch_host_run(h_pixels, n, tol, max_iter, nullptr, h_warm, 0, 0, h_out, h_reports,
+                          static_cast<cudaStream_t>(stream), nullptr);
 }
 
 extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t n, int32_t subspace_iters,

@@ -148,6 +148,14 @@ cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem
 // The per-pixel constants of a work list (one thread per pixel); launch_batch
 // and launch_spectral run it before their kernels.
 cudaError_t launch_pixel_const(const PixelDev *px, int n, PixelConst *out, cudaStream_t s);
+
+// Host-buffer batch shared by the plain and learned host entry points: pmfs
+// into h_out (packed in caller order), reports into h_reports (may be NULL);
+// the warm start is d_warm (device, warm_kind / warm_ld as the batch options),
+// or h_warm (host weights), or none.
+spl_status_t batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
+                            const float *d_warm, const float *h_warm, int warm_kind, int warm_ld, float *h_out,
+                            spl_report_t *h_reports, cudaStream_t s, const spl_batch_opts_t *opts);
 cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem, cudaStream_t s);
 
 cudaError_t launch_chain_flux(const PixelDev &p, float *w, float *u, float *lam, double *F, double *scal,

@@ -909,14 +909,8 @@ extern "C" spl_status_t spl_gemm_bf16(const void *d_A, const void *d_B, int32_t 
 // The logits buffer of the last spl_mlp_forward, [n][2048] (device, owned by m).
 extern "C" const float *spl_mlp_logits(spl_mlp_t *m) { return m ? m->logits : nullptr; }
 
-extern "C" spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, double tol,
-                                                     int32_t max_iter, float *d_out, const int64_t *d_offsets,
-                                                     spl_report_t *h_reports, void *stream,
-                                                     const spl_batch_opts_t *opts) {
-    if (!m || n < 1 || !h_pixels) return SPL_EINVAL;
-    if (stream != static_cast<void *>(m->stream)) return SPL_EINVAL;
-    // Logits of the whole batch, produced chunk by chunk (max_batch rows at a
-    // time) into a buffer of n rows owned by the network.
+// Logits of the whole batch into m->warm, chunk by chunk (max_batch rows at a time).
+static spl_status_t learned_logits(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n) {
     const size_t rows = (size_t)padM(n);
     if (m->warm_cap < rows) {
         if (m->warm) cudaFree(m->warm);
@@ -934,6 +928,36 @@ extern "C" spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pix
         if ((st = upload_pixels(m, h_pixels + k0, c)) != SPL_OK) return st;
         if ((st = forward(m, c, false, m->warm + (size_t)k0 * kOutPad)) != SPL_OK) return st;
     }
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n,
+                                                          double tol, int32_t max_iter, float *h_out,
+                                                          spl_report_t *h_reports, void *stream,
+                                                          const spl_batch_opts_t *opts) {
+    if (!m || n < 1 || !h_pixels || !h_out) return SPL_EINVAL;
+    if (stream != static_cast<void *>(m->stream)) return SPL_EINVAL;
+    spl_status_t st = learned_logits(m, h_pixels, n);
+    if (st != SPL_OK) return st;
+    st = batch_host_run(h_pixels, n, tol, max_iter, m->warm, nullptr, SPL_WARM_LEARNED, kOutPad, h_out, h_reports,
+                        m->stream, opts);
+    if (st == SPL_OK || st == SPL_ENOCONV) {
+        int h = 0;
+        MCU(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+        MCU(cudaStreamSynchronize(m->stream));
+        if (h) return SPL_ETIMEOUT;
+    }
+    return st;
+}
+
+extern "C" spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n, double tol,
+                                                     int32_t max_iter, float *d_out, const int64_t *d_offsets,
+                                                     spl_report_t *h_reports, void *stream,
+                                                     const spl_batch_opts_t *opts) {
+    if (!m || n < 1 || !h_pixels) return SPL_EINVAL;
+    if (stream != static_cast<void *>(m->stream)) return SPL_EINVAL;
+    spl_status_t lst = learned_logits(m, h_pixels, n);
+    if (lst != SPL_OK) return lst;
     spl_batch_opts_t o{};
     if (opts) o = *opts;
     o.warm_kind = SPL_WARM_LEARNED;

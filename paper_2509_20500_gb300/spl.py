@@ -55,7 +55,8 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_batch_stationary_host", "spl_batch_stationary_noalloc", "spl_matrix", "spl_chain_flux", "spl_free", "spl_strerror",
             "spl_last_cuda_error", "spl_version", "spl_mlp_create", "spl_mlp_param_count", "spl_mlp_set_params",
             "spl_mlp_get_params", "spl_mlp_get_state", "spl_mlp_set_state", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
-            "spl_mlp_free", "spl_batch_stationary_learned", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
+            "spl_mlp_free", "spl_batch_stationary_learned",
+            "spl_batch_stationary_learned_host", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
 
 _lib = None
@@ -144,6 +145,9 @@ def lib():
         L.spl_batch_stationary_learned.argtypes = [vp, P, i32, f64, i32, vp, vp, ctypes.POINTER(spl_report_t), vp,
                                                    ctypes.POINTER(spl_batch_opts_t)]
         L.spl_batch_stationary_learned.restype = ctypes.c_int
+        L.spl_batch_stationary_learned_host.argtypes = [vp, P, i32, f64, i32, vp, ctypes.POINTER(spl_report_t), vp,
+                                                        ctypes.POINTER(spl_batch_opts_t)]
+        L.spl_batch_stationary_learned_host.restype = ctypes.c_int
         L.spl_batch_spectral.argtypes = [ctypes.POINTER(spl_pixel_t), i32, i32, vp, vp]
         L.spl_batch_spectral.restype = ctypes.c_int
         L.spl_mc_histograms.argtypes = [ctypes.POINTER(spl_pixel_t), i32, i32, ctypes.c_int64, ctypes.c_uint64, vp,
@@ -394,14 +398,14 @@ def batch_kernel_ms() -> float:
 
 
 def batch_stationary_host(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm: np.ndarray | None = None,
-                          out: np.ndarray | None = None, reports: bool = True, stream=None):
+                          out: np.ndarray | None = None, reports: bool = True, stream=None, c_pixels=None):
     """spl_batch_stationary_host: host buffers in and out (copies inside the call)."""
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
     n = len(px)
     off = offsets_of(px)
     if out is None:
         out = np.empty(int(off[-1]), dtype=np.float32)
-    arr = pixels_to_c(px)
+    arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
     wp = None if warm is None else ctypes.c_void_p(np.ascontiguousarray(warm, dtype=np.float32).ctypes.data)
     st = lib().spl_batch_stationary_host(arr, n, float(tol), int(max_iter), wp, ctypes.c_void_p(out.ctypes.data),
@@ -504,6 +508,25 @@ class MLP:
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
                                                 _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))
+        return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+    def batch_stationary_host(self, px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, out=None,
+                              reports: bool = True, c_pixels=None, pass_kind: int = SPL_PASS_DENSE,
+                              flux_kind: int = SPL_FLUX_POINT, tune: int = 0):
+        """spl_batch_stationary_learned_host: pmfs into a host tensor `out`
+        (pinned if allocated here), packed in caller order."""
+        import torch
+        n = len(px)
+        off = offsets_of(px)
+        if out is None:
+            out = torch.empty(int(off[-1]), dtype=torch.float32).pin_memory()
+        reps = (spl_report_t * max(1, n))() if reports else None
+        arr = pixels_to_c(px) if c_pixels is None else c_pixels
+        opts = spl_batch_opts_t(0, 0, 1, 0, 0, int(pass_kind), int(flux_kind), int(tune), -1)
+        st = lib().spl_batch_stationary_learned_host(self._m, arr, n, float(tol), int(max_iter),
+                                                     ctypes.c_void_p(out.data_ptr()), reps, self._stream,
+                                                     ctypes.byref(opts))
+        _check(st, "spl_batch_stationary_learned_host", (SPL_OK, SPL_ENOCONV))
         return out, off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
 
     def close(self):

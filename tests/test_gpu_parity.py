@@ -450,6 +450,23 @@ def test_batch_host_entry_point(spl):
     np.testing.assert_array_equal(h, d.cpu().numpy())
 
 
+@pytest.mark.parametrize("kind", ["one size", "ragged"])
+def test_batch_host_entry_point_ranges(spl, kind):
+    """A batch of one size large enough for four ranges (copies overlapped
+    with compute) and a ragged one (one launch): the host entry point gives
+    the device path's pmfs and reports bit for bit."""
+    if kind == "one size":
+        px = W.array_pixels(6000, seed=16, n_bins=700)
+    else:
+        px = np.concatenate([W.array_pixels(3000, seed=17, n_bins=700), W.random_small(40, seed=18, n_max=300)])
+    d, off, rd = spl.batch_stationary(px)
+    h, off2, rh = spl.batch_stationary_host(px)
+    np.testing.assert_array_equal(off, off2)
+    np.testing.assert_array_equal(h, d.cpu().numpy())
+    for k in ("iters", "status"):
+        np.testing.assert_array_equal(rh[k], rd[k])
+
+
 def test_batch_lambda2_estimates(spl):
     """The |lambda_2| and phase the stop rule estimates track LAPACK's
     eigenvalues of P~ (Sec. 4) for pixels whose subdominant mode is separated."""
