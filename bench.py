@@ -531,6 +531,23 @@ def run_gpu(args):
         hr["fused_ms_per_pdf"] = pdf_wall_ms(ch)
         ch.close()
         hr["timing"] = "passes and steps replayed from one captured CUDA graph (no host launch overhead)"
+        # the dead-time and signal sweep of the single-pixel workload (12 pixels)
+        sweep = []
+        for k, q in enumerate(W.highres()):
+            q = q.reshape(1)
+            row = {"t_d": float(q["t_d"][0]), "S": float(q["S"][0])}
+            for mode, key in ((spl.SPL_MATERIALIZED, "materialized"), (spl.SPL_FUSED, "fused")):
+                c = spl.Chain(q, mode)
+                _, rr = c.stationary(tol=TOL)
+                row[key + "_iters"] = int(rr["iters"])
+                row[key + "_status"] = int(rr["status"])
+                row[key + "_ms_per_pdf"] = pdf_wall_ms(c, reps=5)
+                c.close()
+            sweep.append(row)
+        hr["sweep"] = {"pixels": sweep,
+                       "fused_ms_per_pdf_median": statistics.median(r["fused_ms_per_pdf"] for r in sweep),
+                       "materialized_ms_per_pdf_median": statistics.median(r["materialized_ms_per_pdf"] for r in sweep),
+                       "workload": "N = 10000, t_d in {10, 40, 75, 130}, tau = 30, sigma = 0.3, S in {0.05, 0.5, 5}, B = 0.5"}
         extra["highres_n10000"] = hr
 
     # end to end through the public API: pixel list from host memory (copied

@@ -148,10 +148,11 @@ def test_chain_warm_start_from_answer(spl):
     ch.close()
 
 
-@pytest.mark.parametrize("t_d", [10.0, 130.0])
-def test_highres_materialized_and_fused(spl, t_d):
-    """N = 10000 (400 MB FP32 matrix): both paths agree with the oracle."""
-    px = W.pixel(10000, t_d, 30.0, 0.3, 5.0, 0.5)
+@pytest.mark.parametrize("t_d,S", [(10.0, 5.0), (130.0, 5.0), (40.0, 0.05), (75.0, 0.5)])
+def test_highres_materialized_and_fused(spl, t_d, S):
+    """N = 10000 (400 MB FP32 matrix), points of the dead-time and signal
+    sweep: both paths agree with the oracle."""
+    px = W.pixel(10000, t_d, 30.0, 0.3, S, 0.5)
     p = _dict(px)
     ref = oracle.batch_stationary([p], tol=1e-12)[0]
     for mode in (spl.SPL_MATERIALIZED, spl.SPL_FUSED):
