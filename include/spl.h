@@ -27,6 +27,12 @@
  *  - Results are FP32 pmfs (sum 1).  Matrix entries and power iterations run
  *    in FP32; the cumulative flux F, Lambda and the exponentials that turn them
  *    into per-bin factors run in FP64 on the GPU.
+ *  - Threads: the batch calls of one device share the library's workspace for
+ *    that device and take its lock, so they may come from several host
+ *    threads (they run one at a time; spl_batch_stationary_noalloc shares one
+ *    static scratch area instead, see there).  A chain (spl_chain_t) or a
+ *    network (spl_mlp_t) is used by one thread at a time; distinct objects are
+ *    independent.
  */
 #ifndef SPL_H
 #define SPL_H
