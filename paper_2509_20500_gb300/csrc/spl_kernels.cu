@@ -114,15 +114,15 @@ __device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[
 // ~15 for one sequential 2000-term chain.
 template <int C, int KC = kChain>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
-                                        float (&acc)[C], float (&comp)[C]) {
+                                        float (&acc)[C], float (&comp)[C], int kc = KC) {
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
 #if SPL_FFMA2
     static_assert(kNch == 4, "packed form keeps four chains per output");
     float2 mm[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) mm[c] = make_float2(m[c], m[c]);
-    for (int b0 = lo; b0 < hi; b0 += KC) {
-        const int q1 = (min(hi, b0 + KC) - b0) >> 2;
+    for (int b0 = lo; b0 < hi; b0 += kc) {
+        const int q1 = (min(hi, b0 + kc) - b0) >> 2;
         float2 in01[C], in23[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) { in01[c] = make_float2(0.f, 0.f); in23[c] = make_float2(0.f, 0.f); }
@@ -141,8 +141,8 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
             fast_two_sum_acc(acc[c], comp[c], (in01[c].x + in01[c].y) + (in23[c].x + in23[c].y));
     }
 #else
-    for (int b0 = lo; b0 < hi; b0 += KC) {
-        const int q1 = (min(hi, b0 + KC) - b0) >> 2;
+    for (int b0 = lo; b0 < hi; b0 += kc) {
+        const int q1 = (min(hi, b0 + kc) - b0) >> 2;
         float in[kNch][C];
         chains_zero<C>(in);
 #pragma unroll 8
@@ -176,70 +176,71 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // a 32-entry block boundary (b_hi a multiple of 32 then).
 template <int C, bool kRowPass, int KC = kChain, bool kLoCut = false>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
-                                         const float (&mlo)[C], const float (&mhi)[C], float (&out)[C]) {
+                                         const float (&mlo)[C], const float (&mhi)[C], float (&out)[C],
+                                         int kc = KC) {
     float acc[C], comp[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) { acc[c] = 0.f; comp[c] = 0.f; }
     const int span_end = base + 32 * C;
-    // below the span: b < a for every owned a
-    {
-        float m[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) m[c] = kRowPass ? mhi[c] : mlo[c];
-        tri_run<C, KC>(v, b_lo, min(b_hi, base), m, acc, comp);
-    }
-    // the span itself (32 C entries, added as chunks of at most kChain)
-    if ((kLoCut ? base + 32 * C > b_lo : base >= b_lo) && base < b_hi) {
-        const float4 *v4 = reinterpret_cast<const float4 *>(v);
-        float in[kNch][C];
-        chains_zero<C>(in);
-#pragma unroll
-        for (int cb = 0; cb < C; ++cb) {
-            // weights of the columns that are uniform over this block
+    // below the span (part 0: b < a for every owned a), the span itself
+    // (part 1), above the span (part 2: b > a); one copy of each piece of
+    // code, in this order
+#pragma unroll 1
+    for (int part = 0; part < 3; ++part) {
+        if (part != 1) {
+            const bool below = part == 0;
             float m[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const bool near = kRowPass ? (c < cb) : (c > cb);
-                m[c] = near ? mlo[c] : mhi[c];
-            }
-            // blocks outside [b_lo, b_hi) (only where the span is cut) add nothing
-            const bool in_range = base + 32 * cb < b_hi && (!kLoCut || base + 32 * cb >= b_lo);
-#pragma unroll 2
-            for (int q = 0; q < (in_range ? 8 : 0); ++q) {
-                const float4 x = v4[((base + 32 * cb) >> 2) + q];
-                const int t = 4 * q;   // offset of x.x inside the block
-#pragma unroll
+            for (int c = 0; c < C; ++c) m[c] = (below != kRowPass) ? mlo[c] : mhi[c];
+            tri_run<C, KC>(v, below ? b_lo : max(b_lo, span_end), below ? min(b_hi, base) : b_hi, m, acc, comp, kc);
+            continue;
+        }
+        // the span itself (32 C entries, added as chunks of at most kChain)
+        if ((kLoCut ? base + 32 * C > b_lo : base >= b_lo) && base < b_hi) {
+            const float4 *v4 = reinterpret_cast<const float4 *>(v);
+            float in[kNch][C];
+            chains_zero<C>(in);
+    #pragma unroll
+            for (int cb = 0; cb < C; ++cb) {
+                // weights of the columns that are uniform over this block
+                float m[C];
+    #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    if (c == cb) {
-                        // per-entry triangle weight of the owned column
-                        const bool n0 = kRowPass ? (t + 0 >= lane) : (t + 0 <= lane);
-                        const bool n1 = kRowPass ? (t + 1 >= lane) : (t + 1 <= lane);
-                        const bool n2 = kRowPass ? (t + 2 >= lane) : (t + 2 <= lane);
-                        const bool n3 = kRowPass ? (t + 3 >= lane) : (t + 3 <= lane);
-                        in[0 % kNch][c] = fmaf(x.x, n0 ? mlo[c] : mhi[c], in[0 % kNch][c]);
-                        in[1 % kNch][c] = fmaf(x.y, n1 ? mlo[c] : mhi[c], in[1 % kNch][c]);
-                        in[2 % kNch][c] = fmaf(x.z, n2 ? mlo[c] : mhi[c], in[2 % kNch][c]);
-                        in[3 % kNch][c] = fmaf(x.w, n3 ? mlo[c] : mhi[c], in[3 % kNch][c]);
-                    } else {
-                        in[0 % kNch][c] = fmaf(x.x, m[c], in[0 % kNch][c]);
-                        in[1 % kNch][c] = fmaf(x.y, m[c], in[1 % kNch][c]);
-                        in[2 % kNch][c] = fmaf(x.z, m[c], in[2 % kNch][c]);
-                        in[3 % kNch][c] = fmaf(x.w, m[c], in[3 % kNch][c]);
+                    const bool near = kRowPass ? (c < cb) : (c > cb);
+                    m[c] = near ? mlo[c] : mhi[c];
+                }
+                // blocks outside [b_lo, b_hi) (only where the span is cut) add nothing
+                const bool in_range = base + 32 * cb < b_hi && (!kLoCut || base + 32 * cb >= b_lo);
+    #pragma unroll 2
+                for (int q = 0; q < (in_range ? 8 : 0); ++q) {
+                    const float4 x = v4[((base + 32 * cb) >> 2) + q];
+                    const int t = 4 * q;   // offset of x.x inside the block
+    #pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        if (c == cb) {
+                            // per-entry triangle weight of the owned column
+                            const bool n0 = kRowPass ? (t + 0 >= lane) : (t + 0 <= lane);
+                            const bool n1 = kRowPass ? (t + 1 >= lane) : (t + 1 <= lane);
+                            const bool n2 = kRowPass ? (t + 2 >= lane) : (t + 2 <= lane);
+                            const bool n3 = kRowPass ? (t + 3 >= lane) : (t + 3 <= lane);
+                            in[0 % kNch][c] = fmaf(x.x, n0 ? mlo[c] : mhi[c], in[0 % kNch][c]);
+                            in[1 % kNch][c] = fmaf(x.y, n1 ? mlo[c] : mhi[c], in[1 % kNch][c]);
+                            in[2 % kNch][c] = fmaf(x.z, n2 ? mlo[c] : mhi[c], in[2 % kNch][c]);
+                            in[3 % kNch][c] = fmaf(x.w, n3 ? mlo[c] : mhi[c], in[3 % kNch][c]);
+                        } else {
+                            in[0 % kNch][c] = fmaf(x.x, m[c], in[0 % kNch][c]);
+                            in[1 % kNch][c] = fmaf(x.y, m[c], in[1 % kNch][c]);
+                            in[2 % kNch][c] = fmaf(x.z, m[c], in[2 % kNch][c]);
+                            in[3 % kNch][c] = fmaf(x.w, m[c], in[3 % kNch][c]);
+                        }
                     }
                 }
-            }
-            if (((cb + 1) * 32) % KC == 0 || cb == C - 1) {
-                chains_flush<C>(in, acc, comp);
-                chains_zero<C>(in);
+                if (((cb + 1) * 32) % kc == 0 || cb == C - 1) {
+                    chains_flush<C>(in, acc, comp);
+                    chains_zero<C>(in);
+                }
             }
         }
-    }
-    // above the span: b > a for every owned a
-    {
-        float m[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) m[c] = kRowPass ? mlo[c] : mhi[c];
-        tri_run<C, KC>(v, max(b_lo, span_end), b_hi, m, acc, comp);
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) out[c] = acc[c] + comp[c];
@@ -645,10 +646,8 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                         mlo[c] = w;
                         mhi[c] = w * eL;
                     }
-                    if (fine)
-                        tri_pass<C, false, kChain>(sv, 0, nrow, base, lane, mlo, mhi, y);
-                    else
-                        tri_pass<C, false, kChainCoarse>(sv, 0, nrow, base, lane, mlo, mhi, y);
+                    // one code path for both chunk lengths (only the outer step differs)
+                    tri_pass<C, false>(sv, 0, nrow, base, lane, mlo, mhi, y, fine ? kChain : kChainCoarse);
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
                         const int j = base + 32 * c + lane;
