@@ -200,22 +200,22 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
             const float4 *v4 = reinterpret_cast<const float4 *>(v);
             float in[kNch][C];
             chains_zero<C>(in);
-    #pragma unroll
+#pragma unroll
             for (int cb = 0; cb < C; ++cb) {
                 // weights of the columns that are uniform over this block
                 float m[C];
-    #pragma unroll
+#pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const bool near = kRowPass ? (c < cb) : (c > cb);
                     m[c] = near ? mlo[c] : mhi[c];
                 }
                 // blocks outside [b_lo, b_hi) (only where the span is cut) add nothing
                 const bool in_range = base + 32 * cb < b_hi && (!kLoCut || base + 32 * cb >= b_lo);
-    #pragma unroll 2
+#pragma unroll 2
                 for (int q = 0; q < (in_range ? 8 : 0); ++q) {
                     const float4 x = v4[((base + 32 * cb) >> 2) + q];
                     const int t = 4 * q;   // offset of x.x inside the block
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < C; ++c) {
                         if (c == cb) {
                             // per-entry triangle weight of the owned column
