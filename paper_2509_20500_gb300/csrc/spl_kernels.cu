@@ -57,6 +57,12 @@ namespace spl {
 #ifndef SPL_FFMA2
 #define SPL_FFMA2 1
 #endif
+// Unroll depth of the uniform-weight loop (float4 steps); deeper hides more
+// shared-memory latency, shallower keeps the hot code small.
+#ifndef SPL_TRI_UNROLL
+#define SPL_TRI_UNROLL 8
+#endif
+constexpr int kTriUnroll = SPL_TRI_UNROLL;
 constexpr int kChain = SPL_KCHAIN;
 // Chunk length where the summed vector is spread out (the row pass, and
 // column passes whose iterate has sum_j pi_j^2 <= kFineIpr): there 256-row
@@ -126,7 +132,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         float2 in01[C], in23[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) { in01[c] = make_float2(0.f, 0.f); in23[c] = make_float2(0.f, 0.f); }
-#pragma unroll 8
+#pragma unroll kTriUnroll
         for (int q = 0; q < q1; ++q) {
             const float4 x = v4[(b0 >> 2) + q];
             const float2 xa = make_float2(x.x, x.y), xb = make_float2(x.z, x.w);
@@ -145,7 +151,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         const int q1 = (min(hi, b0 + kc) - b0) >> 2;
         float in[kNch][C];
         chains_zero<C>(in);
-#pragma unroll 8
+#pragma unroll kTriUnroll
         for (int q = 0; q < q1; ++q) {
             const float4 x = v4[(b0 >> 2) + q];
 #pragma unroll
