@@ -124,15 +124,24 @@ class ClockSampler:
 
 
 def batch_kernel_source_hash() -> str:
-    """Hash of the batch kernel's source (spl_kernels.cu up to the end of its
-    section, with the pass helpers it uses, plus spl_device.cuh), used to tell whether a stored ncu traffic figure still
+    """Hash of the batch kernel's code (spl_kernels.cu up to the end of its
+    section, with the pass helpers it uses, plus spl_device.cuh; comments and
+    blank space left out), used to tell whether a stored ncu traffic figure still
     describes the kernel being timed."""
     import hashlib
+    import re
+
+    def code_only(t: str) -> str:
+        # comments and blank space do not change the kernel
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        return "\n".join(line.strip() for line in t.splitlines() if line.strip())
+
     base = os.path.join(ROOT, "paper_2509_20500_gb300", "csrc")
     txt = open(os.path.join(base, "spl_kernels.cu")).read()
     b = txt.index("// K1 for a single chain: per-bin vectors")
-    h = hashlib.sha256(txt[:b].encode())      # the batch kernel and every device function before it
-    h.update(open(os.path.join(base, "spl_device.cuh")).read().encode())
+    h = hashlib.sha256(code_only(txt[:b]).encode())      # the batch kernel and every device function before it
+    h.update(code_only(open(os.path.join(base, "spl_device.cuh")).read()).encode())
     return h.hexdigest()[:16]
 
 

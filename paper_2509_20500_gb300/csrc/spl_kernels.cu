@@ -113,11 +113,12 @@ __device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[
     }
 }
 
-// Uniform-weight run over b in [lo, hi) (multiples of 4).  Each kChain-long
-// chunk is summed in kNch interleaved FFMA chains (float4 lane e feeds chain
-// e % kNch), which are then added into the compensated outer accumulator:
-// relative rounding error per output about one FP32 unit roundoff instead of
-// ~15 for one sequential 2000-term chain.
+// Uniform-weight run over b in [lo, hi) (multiples of 4).  Each chunk of kc
+// rows (the template default KC, or a runtime value so that one copy of the
+// code serves several chunk lengths) is summed in kNch interleaved FFMA
+// chains (float4 lane e feeds chain e % kNch), which are then added into the
+// compensated outer accumulator: relative rounding error per output about
+// one FP32 unit roundoff instead of ~15 for one sequential 2000-term chain.
 template <int C, int KC = kChain>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
                                         float (&acc)[C], float (&comp)[C], int kc = KC) {
@@ -179,7 +180,9 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // for a chunk).  All bounds are multiples of 4; the span either starts at or
 // after b_lo, or lies fully below it (with kLoCut: b_lo may also fall inside
 // the span at a 32-entry block boundary); a span reaching past b_hi is cut at
-// a 32-entry block boundary (b_hi a multiple of 32 then).
+// a 32-entry block boundary (b_hi a multiple of 32 then).  kc is the chunk
+// length (see tri_run); the pieces below, inside and above the span run as
+// one loop so that each is one copy of code.
 template <int C, bool kRowPass, int KC = kChain, bool kLoCut = false>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C],
