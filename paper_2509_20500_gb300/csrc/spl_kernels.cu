@@ -181,9 +181,11 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
 // after b_lo, or lies fully below it (with kLoCut: b_lo may also fall inside
 // the span at a 32-entry block boundary); a span reaching past b_hi is cut at
 // a 32-entry block boundary (b_hi a multiple of 32 then).  kc is the chunk
-// length (see tri_run); the pieces below, inside and above the span run as
-// one loop so that each is one copy of code.
-template <int C, bool kRowPass, int KC = kChain, bool kLoCut = false>
+// length (see tri_run).  kOneCopy runs the pieces below, inside and above the
+// span as one loop, each one copy of code (the batch kernel, where hot-code
+// size matters); otherwise they are inlined one after the other (the
+// single-chain kernels, whose warps each see only a few row blocks).
+template <int C, bool kRowPass, int KC = kChain, bool kLoCut = false, bool kOneCopy = true>
 __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, int b_hi, int base, int lane,
                                          const float (&mlo)[C], const float (&mhi)[C], float (&out)[C],
                                          int kc = KC) {
@@ -194,15 +196,14 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
     // below the span (part 0: b < a for every owned a), the span itself
     // (part 1), above the span (part 2: b > a); one copy of each piece of
     // code, in this order
-#pragma unroll 1
-    for (int part = 0; part < 3; ++part) {
+    auto piece = [&](int part) {
         if (part != 1) {
             const bool below = part == 0;
             float m[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) m[c] = (below != kRowPass) ? mlo[c] : mhi[c];
             tri_run<C, KC>(v, below ? b_lo : max(b_lo, span_end), below ? min(b_hi, base) : b_hi, m, acc, comp, kc);
-            continue;
+            return;
         }
         // the span itself (32 C entries, added as chunks of at most kChain)
         if ((kLoCut ? base + 32 * C > b_lo : base >= b_lo) && base < b_hi) {
@@ -250,6 +251,14 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
                 }
             }
         }
+    };
+    if constexpr (kOneCopy) {
+#pragma unroll 1
+        for (int part = 0; part < 3; ++part) piece(part);
+    } else {
+        piece(0);
+        piece(1);
+        piece(2);
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) out[c] = acc[c] + comp[c];
@@ -1193,7 +1202,7 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
         mlo[c] = m;
         mhi[c] = m * eL;
     }
-    tri_pass<C, kRowPass>(sv - b0, b0, b1, wbase, lane, mlo, mhi, out);
+    tri_pass<C, kRowPass, kChain, false, false>(sv - b0, b0, b1, wbase, lane, mlo, mhi, out);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = wbase + 32 * c + lane;
@@ -1454,7 +1463,8 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
                 if (wb1 > wb0) {
                     const float *vt = sv + ((long long)t * RB - wu0) * 32;   // row r of tile t at vt[r]
                     float out[kRunC];
-                    tri_pass<kRunC, false, kChain, true>(vt, 32 * wb0, 32 * wb1, t * kRunTW, lane, mlo, mhi, out);
+                    tri_pass<kRunC, false, kChain, true, false>(vt, 32 * wb0, 32 * wb1, t * kRunTW, lane, mlo, mhi,
+                                                               out);
 #pragma unroll
                     for (int c = 0; c < kRunC; ++c) acc[c] += out[c];
                 }
