@@ -1,0 +1,56 @@
+"""Host logic of bench.py that needs no GPU: the key under which the batch
+kernel's measured DRAM traffic is stored changes with the kernel's code but
+not with its comments or blank space, and the stored figure is returned only
+while the key matches."""
+import importlib.util
+import json
+import os
+import shutil
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench_at(root):
+    spec = importlib.util.spec_from_file_location("bench_copy", os.path.join(root, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    return b
+
+
+def _copy_tree(tmp_path):
+    dst = tmp_path / "repo"
+    os.makedirs(dst / "paper_2509_20500_gb300" / "csrc")
+    os.makedirs(dst / "profiles")
+    shutil.copy(os.path.join(ROOT, "bench.py"), dst / "bench.py")
+    for f in ("spl_kernels.cu", "spl_device.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_2509_20500_gb300", "csrc", f), dst / "paper_2509_20500_gb300" / "csrc" / f)
+    shutil.copy(os.path.join(ROOT, "profiles", "batch_fused_kernel_traffic.json"),
+                dst / "profiles" / "batch_fused_kernel_traffic.json")
+    return dst
+
+
+def test_stored_traffic_matches_the_committed_kernel():
+    b = _bench_at(ROOT)
+    d = json.load(open(os.path.join(ROOT, "profiles", "batch_fused_kernel_traffic.json")))
+    assert d["source_hash"] == b.batch_kernel_source_hash()
+    for arm in ("plain", "learned"):
+        t = b.stored_traffic(arm)
+        a = d["arms"][arm]
+        assert t == a["dram_bytes_read_per_launch"] + a["dram_bytes_write_per_launch"]
+        # no re-reads: within 3 % of the algorithmic bytes of a launch
+        assert abs(t / a["algorithmic_bytes_per_launch"] - 1.0) < 0.03
+
+
+def test_comment_edits_keep_the_key_and_code_edits_drop_it(tmp_path):
+    dst = _copy_tree(tmp_path)
+    b = _bench_at(str(dst))
+    k = dst / "paper_2509_20500_gb300" / "csrc" / "spl_kernels.cu"
+    h0 = b.batch_kernel_source_hash()
+    src = k.read_text()
+    i = src.index("constexpr int kChain = SPL_KCHAIN;")
+    k.write_text(src[:i] + "// a new comment line\n\n" + src[i:])
+    assert b.batch_kernel_source_hash() == h0
+    assert b.stored_traffic("learned") is not None
+    k.write_text(src[:i] + "constexpr int kUnused = 1;\n" + src[i:])
+    assert b.batch_kernel_source_hash() != h0
+    assert b.stored_traffic("learned") is None
