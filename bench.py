@@ -36,9 +36,8 @@ UNIT = "PDFs/s"
 TOL = 1e-6
 MAX_ITER = 1000
 WORKLOAD = "array256: 256x256 pixels, N=2000, t_r=100ns, t_d=75ns, tau~U[5,95], sigma~U[0.2,1], S,B~logU[0.01,5], seed 5"
-SM_COUNT = 152
-FP32_LANES = 128           # FP32 FMA lanes per SM
-SM_MAX_MHZ = 2070.0        # maximum SM clock
+FP32_LANES = 128           # FP32 FMA lanes per SM (nominal peak, context only)
+SM_MAX_MHZ = 2070.0        # maximum SM clock (nominal peak, context only)
 
 
 def dist_env():
@@ -266,6 +265,11 @@ def run_gpu(args):
     build.build()
     spl.lib()
     peaks = measured_peaks() or {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # FP32 roofline denominator: the library's FMA-throughput kernel, measured
+    # here (launches of about the batch kernel's length, median of five)
+    fma = spl.fp32_fma_peak(iters=800_000, reps=5)
+    assert fma["sms"] == sms
 
     # each rank owns an independent 65536-pixel array (weak scaling, no collective)
     px = rank_workload(rank, args.pixels)
@@ -337,7 +341,8 @@ def run_gpu(args):
     flop = float(2.0 * np.sum(N2 * (1 + reps["iters"])))
     kms = statistics.median(kern_ms)
     achieved = flop / (kms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fma["tflops_median"]
+    peak_nominal = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     arm = "learned" if learned else "plain"
     traffic = stored_traffic(arm) if n == 65536 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -346,9 +351,11 @@ def run_gpu(args):
             "bytes_basis": "pmf write (4 B per bin)" + (" + learned logits read (4 B per bin)" if learned else "")
                            + " + 40 B of parameters per pixel", "arm": arm,
             "work": "2 FLOP x N^2 x (1 + iters) per pixel (row pass + power steps, one FFMA per entry)",
-            "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock), derived"}
-    if clocks.get("sm_mhz"):
-        roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+            "peak_basis": "of measured: spl_fp32_fma_peak (16 FMA chains per thread, 4 x 256 threads per SM, "
+                          "median of 5 launches of ~50 ms) in this run",
+            "peak_fp32_best_of_5": fma["tflops_best"], "sms": sms,
+            "peak_nominal": peak_nominal,
+            "peak_nominal_basis": f"{sms} SMs x 128 FP32 FMA lanes x 2 FLOP x 2070 MHz (max SM clock)"}
 
     # accuracy audit of the timed outputs: sampled pixels against the FP64 oracle
     line_audit = None
@@ -357,8 +364,10 @@ def run_gpu(args):
         idx = W.sample_indices(n, args.audit, seed=91)
         refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
         o = out.cpu().numpy().astype(np.float64)
-        errs = [float(np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum()) for r, k in enumerate(idx)]
+        dif = [np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]) for r, k in enumerate(idx)]
+        errs = [float(d.sum()) for d in dif]
         line_audit = {"sampled_pixels": len(idx), "max_l1": max(errs), "mean_l1": float(np.mean(errs)),
+                      "max_abs": max(float(d.max()) for d in dif),
                       "tol": TOL, "of": "the last timed step's output"}
 
     extra = {}
@@ -379,6 +388,20 @@ def run_gpu(args):
     extra["plain"] = {"value": world * n / (plain_ms / 1e3), "ms_per_step": plain_ms,
                       "iters_mean": float(reps_plain["iters"].mean()), "iters_max": int(reps_plain["iters"].max()),
                       "kernel_ms": statistics.median(plain_kern)}
+
+    # the allocation-free entry point on the same pixels (plain start): what
+    # its fixed scratch and default launch shape cost against the plain arm
+    if not args.no_noalloc:
+        def na_step():
+            return spl.batch_stationary_noalloc(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off,
+                                                reports=False, c_pixels=c_px)
+        for _ in range(args.warmup):
+            na_step()
+        na_ms, _ = timed_steps(na_step, args.steps, flush, stream)
+        na = statistics.mean(na_ms)
+        extra["noalloc"] = {"value": world * n / (na / 1e3), "ms_per_step": na,
+                            "vs_plain_batch": plain_ms / na,
+                            "what": "spl_batch_stationary_noalloc, uniform start, same 65536 pixels"}
 
     # the O(N) structured form of the same power step (reported beside the
     # dense path, never as its number): plain and learned starts
@@ -540,23 +563,41 @@ def run_gpu(args):
         hr["fused_ms_per_pdf"] = pdf_wall_ms(ch)
         ch.close()
         hr["timing"] = "passes and steps replayed from one captured CUDA graph (no host launch overhead)"
-        # the dead-time and signal sweep of the single-pixel workload (12 pixels)
+        # the dead-time and signal sweep of the single-pixel workload (12 pixels),
+        # each result against the FP64 oracle (L1 and max-abs)
+        hx = W.highres()
+        hrefs = None
+        if not args.no_cpu_baseline:
+            import oracle
+            ro, rof, _, _ = oracle.batch_stationary(W.as_dicts(hx), tol=1e-12, nthreads=min(6, os.cpu_count() or 1))
+            hrefs = [ro[rof[k]:rof[k + 1]] for k in range(len(hx))]
         sweep = []
-        for k, q in enumerate(W.highres()):
-            q = q.reshape(1)
+        for k in range(len(hx)):
+            q = hx[k:k + 1]
             row = {"t_d": float(q["t_d"][0]), "S": float(q["S"][0])}
             for mode, key in ((spl.SPL_MATERIALIZED, "materialized"), (spl.SPL_FUSED, "fused")):
                 c = spl.Chain(q, mode)
-                _, rr = c.stationary(tol=TOL)
+                pq, rr = c.stationary(tol=TOL)
                 row[key + "_iters"] = int(rr["iters"])
                 row[key + "_status"] = int(rr["status"])
-                row[key + "_ms_per_pdf"] = pdf_wall_ms(c, reps=5)
+                if hrefs is not None:
+                    d = np.abs(pq.cpu().numpy().astype(np.float64) - hrefs[k])
+                    row[key + "_l1"] = float(d.sum())
+                    row[key + "_max_abs"] = float(d.max())
+                row[key + "_wall_ms_per_pdf"] = pdf_wall_ms(c, reps=5)
                 c.close()
             sweep.append(row)
         hr["sweep"] = {"pixels": sweep,
-                       "fused_ms_per_pdf_median": statistics.median(r["fused_ms_per_pdf"] for r in sweep),
-                       "materialized_ms_per_pdf_median": statistics.median(r["materialized_ms_per_pdf"] for r in sweep),
+                       "fused_wall_ms_per_pdf_median": statistics.median(r["fused_wall_ms_per_pdf"] for r in sweep),
+                       "materialized_wall_ms_per_pdf_median":
+                           statistics.median(r["materialized_wall_ms_per_pdf"] for r in sweep),
+                       "wall_ms": "host wall time of one synchronous spl_stationary call (start vector, every step, "
+                                  "stop rule and the report read back), not device time",
                        "workload": "N = 10000, t_d in {10, 40, 75, 130}, tau = 30, sigma = 0.3, S in {0.05, 0.5, 5}, B = 0.5"}
+        if hrefs is not None:
+            for key in ("materialized", "fused"):
+                hr["sweep"][key + "_max_l1"] = max(r[key + "_l1"] for r in sweep)
+                hr["sweep"][key + "_max_abs"] = max(r[key + "_max_abs"] for r in sweep)
         extra["highres_n10000"] = hr
 
     # end to end through the public API: pixel list from host memory (copied
@@ -621,13 +662,64 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, _ = cpu_sample(px, args.cpu_sample)
         rate, dt, used = oracle_rate(sample, os.cpu_count() or 1)
+        rate1, dt1, _ = oracle_rate(sample[:args.cpu_sample_1t], 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
-                                "sample": f"{len(sample)} of the 65536 pixels (seed 55), {dt:.1f} s"}
+                                "sample": f"{len(sample)} of the 65536 pixels (seed 55), {dt:.1f} s",
+                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"the first {min(len(sample), args.cpu_sample_1t)} "
+                                                            f"of those pixels, {dt1:.1f} s"}}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return 0
+
+
+PROFILE_CASES = ("batch_dense", "batch_structured", "gemv", "build", "chain_run", "chain_multi", "fma_peak")
+
+
+def run_profile_case(name: str) -> int:
+    """Small, fixed launch sequences for ncu captures (no timing, no JSON
+    line): each case launches its kernel twice on the same inputs, so a
+    capture with `-k regex:<kernel> -s 1 -c 1` takes a warm, full-size launch.
+      batch_dense / batch_structured: 4096 pixels of the array workload (N = 2000),
+          fixed launch heuristic (no tuning launches), dense or O(N) step;
+      gemv / build / chain_run: one N = 10000 pixel (t_d = 75, S = 0.5), the
+          materialised power step, the materialised build, the fused chain;
+      chain_multi: the 12 pixels of the N = 10000 dead-time and signal sweep
+          in one fused multi-pixel launch;
+      fma_peak: the FP32 FMA throughput kernel."""
+    import torch
+    from paper_2509_20500_gb300 import build, spl, workloads as W
+    build.build()
+    spl.lib()
+    torch.cuda.set_device(0)
+    if name in ("batch_dense", "batch_structured"):
+        px = W.array256()[:4096]
+        pk = spl.SPL_PASS_DENSE if name == "batch_dense" else spl.SPL_PASS_STRUCTURED
+        for _ in range(2):
+            _, _, r = spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, pass_kind=pk, tune=1)
+            assert np.all(r["status"] == 0)
+    elif name in ("gemv", "build", "chain_run"):
+        hp = W.pixel(10000, 75.0, 30.0, 0.3, 0.5, 0.5)
+        ch = spl.Chain(hp, spl.SPL_FUSED if name == "chain_run" else spl.SPL_MATERIALIZED)
+        if name == "build":
+            ch.time_build(1)
+        else:
+            for _ in range(2):
+                _, r = ch.stationary(tol=TOL)
+                assert r["status"] == 0
+        ch.close()
+    elif name == "chain_multi":
+        hx = W.highres()
+        for _ in range(2):
+            _, _, r = spl.chains_stationary(hx, tol=TOL)
+            assert np.all(r["status"] == 0)
+    elif name == "fma_peak":
+        spl.fp32_fma_peak(iters=20_000, reps=1)
+    torch.cuda.synchronize()
+    print(f"profile case {name} done", flush=True)
     return 0
 
 
@@ -639,12 +731,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--ref-sample", type=int, default=128)
+    ap.add_argument("--cpu-sample-1t", type=int, default=48, help="pixels of the single-thread oracle timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pixels", type=int, default=0, help="use only the first P pixels (profiling)")
     ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
     ap.add_argument("--no-highres", action="store_true")
     ap.add_argument("--no-structured", action="store_true")
+    ap.add_argument("--no-noalloc", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-spectral", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
@@ -652,7 +746,10 @@ def main():
     ap.add_argument("--audit", type=int, default=512, help="pixels of the timed output checked against the oracle")
     ap.add_argument("--train-pixels", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--profile-case", choices=PROFILE_CASES, help="run one small launch sequence for ncu and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -257,15 +257,19 @@ SPL_API spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int3
  *   Arguments are those of spl_batch_stationary (d_warm: NULL or packed
  *   nonnegative weights; d_out and d_offsets caller-owned device arrays;
  *   h_reports NULL or host [n]).
- *   The kernel's device scratch (work list, queue counter, reports) is a
- *   fixed file-scope device array of about 4 MB that every GPU loading the
- *   library holds until the process exits; host staging is static too.  No
- *   cudaMalloc, cudaFree or other allocating routine is called.
+ *   The kernel's device scratch (queue counter, work list, reports and the
+ *   per-pixel flux constants) is a fixed file-scope device array of
+ *   15,204,608 bytes (about 15.2 MB) that every GPU loading the library holds
+ *   until the process exits; host staging is static too.  No cudaMalloc,
+ *   cudaFree or other allocating routine is called.
  *   Limits: n <= 65536 pixels and 2 <= n_bins <= 3072 per pixel; larger
  *   requests return SPL_EINVAL before any device work.
  *   The first call on a device looks up the array's device address for that
- *   device (cudaGetSymbolAddress); make that first call before any stream
- *   capture.  All calls share the array and it keeps the previous call's
+ *   device (cudaGetSymbolAddress).  With lazy module loading (the CUDA
+ *   default) that lookup loads the library's module on the device, which is
+ *   when the array is reserved: the first call per device may allocate and
+ *   synchronise the device.  Make it during start-up, before any stream
+ *   capture; later calls allocate nothing.  All calls share the array and it keeps the previous call's
  *   contents (the queue counter is cleared by each call); calls whose work
  *   overlaps on the GPU race on it, so issue them one after the other.
  *   With h_reports the call synchronises `stream`; without, it is
@@ -362,6 +366,19 @@ SPL_API spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t blo
  * device allocation had failed (SPL_ENOMEM); with SPL_FAULT=launch as if its
  * kernel launch had failed (SPL_ECUDA). */
 SPL_API spl_status_t spl_selftest_bounded_waits(void *stream);
+
+/* Measurement: the FP32 FMA throughput of the current device, the
+ * denominator of the FP32 rooflines of the matrix-free passes.  A kernel of
+ * 4 blocks x 256 threads per SM runs 16 independent FMA chains per thread for
+ * `iters` rounds (2 x 16 x iters FLOP per thread); one untimed launch, then
+ * `reps` launches timed one by one with CUDA events on `stream`.
+ * *tflops_median / *tflops_best (may be NULL) get the median and fastest
+ * launch in TFLOP/s, *sms_out (may be NULL) the SM count used.  The paper has
+ * no counterpart: it is the roofline denominator, not part of the method.
+ * SPL_EINVAL for iters < 1, reps < 1 or tflops_median == NULL; SPL_ENOMEM,
+ * SPL_ECUDA. */
+SPL_API spl_status_t spl_fp32_fma_peak(int32_t iters, int32_t reps, void *stream, double *tflops_median,
+                                       double *tflops_best, int32_t *sms_out);
 
 /* The MLP's tensor-core GEMM on its own, for tests: D[M][N] = A[M][K] B[N][K]^T
  * with row-major BF16 device matrices A, B and an FP32 device output D.

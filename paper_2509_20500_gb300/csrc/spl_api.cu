@@ -54,10 +54,12 @@ bool finite_all(const spl_pixel_t &p) {
 constexpr double kLambdaMax = 120.0;
 constexpr int32_t kMaxBins = 1 << 24;
 
+}  // namespace
+
 // a1: validate and derive the row shift.  q = fmod(t_d, t_r) * N / t_r is
 // evaluated in IEEE FP64 in that order (no contraction: a product then a
 // quotient), l = ceil(q) (Theorem 2), reduced modulo N.
-spl_status_t make_pixel(const spl_pixel_t &p, PixelDev &d) {
+spl_status_t spl::make_pixel(const spl_pixel_t &p, PixelDev &d) {
     if (!finite_all(p)) return SPL_EINVAL;
     if (p.n_bins < 2 || p.n_bins > kMaxBins) return SPL_EINVAL;
     if (!(p.t_r > 0.0) || !(p.sigma > 0.0) || p.t_d < 0.0 || p.S < 0.0 || p.B < 0.0) return SPL_EINVAL;
@@ -90,6 +92,8 @@ spl_status_t make_pixel(const spl_pixel_t &p, PixelDev &d) {
     d.pad_ = 0;
     return SPL_OK;
 }
+
+namespace {
 
 int num_sms_current() {
     int dev = 0, sms = 0;
@@ -1225,6 +1229,41 @@ extern "C" spl_status_t spl_batch_kernel_ms(float *ms) {
     if (!ws->timed) return SPL_EINVAL;
     SPL_CU(cudaEventSynchronize(ws->ev1));
     SPL_CU(cudaEventElapsedTime(ms, ws->ev0, ws->ev1));
+    return SPL_OK;
+}
+
+extern "C" spl_status_t spl_fp32_fma_peak(int32_t iters, int32_t reps, void *stream, double *tflops_median,
+                                          double *tflops_best, int32_t *sms_out) {
+    if (iters < 1 || reps < 1 || !tflops_median) return SPL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return note_cuda_error(e, "fma peak: device query");
+    float *out = nullptr;
+    e = cudaMalloc(&out, fma_peak_out_floats(sms) * sizeof(float));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SPL_ENOMEM : note_cuda_error(e, "fma peak: alloc");
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e == cudaSuccess) e = launch_fma_peak(out, sms, iters, s);   // untimed
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(ev[2 * r], s);
+        if (e == cudaSuccess) e = launch_fma_peak(out, sms, iters, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::vector<float> ms((size_t)reps, 0.f);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(out);
+    if (e != cudaSuccess) return note_cuda_error(e, "fma peak");
+    std::sort(ms.begin(), ms.end());
+    const double flop = fma_peak_flop(sms, iters);
+    *tflops_median = flop / (ms[(size_t)reps / 2] * 1e-3) / 1e12;
+    if (tflops_best) *tflops_best = flop / (ms[0] * 1e-3) / 1e12;
+    if (sms_out) *sms_out = sms;
     return SPL_OK;
 }
 

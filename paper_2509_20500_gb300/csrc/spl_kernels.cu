@@ -1612,6 +1612,44 @@ cudaError_t launch_selftest_waits(unsigned *bar, int *err_flag, int *status, cud
 }
 
 // ======================================================================
+// FP32 FMA throughput (the denominator of the FP32 rooflines)
+// ======================================================================
+//
+// Every thread runs kFmaChains independent FMA chains x <- x a + b for `iters`
+// rounds; the chains give each warp enough independent instructions to cover
+// the FMA latency, and the unrolled inner loop keeps the loop overhead a few
+// percent of the issue slots.  4 blocks of 256 threads per SM.  The sum of
+// the chains is written so that no FMA can be removed.  Work per launch:
+// 2 FLOP x kFmaChains x iters x threads.
+
+constexpr int kFmaChains = 16;
+constexpr int kFmaNT = 256;
+
+__global__ void __launch_bounds__(kFmaNT) fma_peak_kernel(float *out, int iters, float a, float b) {
+    float x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = (float)(threadIdx.x + k) * 1e-3f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) sum += x[k];
+    out[(size_t)blockIdx.x * kFmaNT + threadIdx.x] = sum;
+}
+
+int fma_peak_blocks(int sms) { return 4 * sms; }
+double fma_peak_flop(int sms, int iters) { return 2.0 * kFmaChains * (double)iters * fma_peak_blocks(sms) * kFmaNT; }
+size_t fma_peak_out_floats(int sms) { return (size_t)fma_peak_blocks(sms) * kFmaNT; }
+
+cudaError_t launch_fma_peak(float *out, int sms, int iters, cudaStream_t s) {
+    fma_peak_kernel<<<fma_peak_blocks(sms), kFmaNT, 0, s>>>(out, iters, 0.9999999f, 1e-7f);
+    return cudaGetLastError();
+}
+
+// ======================================================================
 // Finish of one power step (whole GPU, two kernels)
 // ======================================================================
 //

@@ -13,6 +13,11 @@ namespace spl {
 // Records a CUDA failure for spl_last_cuda_error; returns SPL_ECUDA.
 spl_status_t note_cuda_error(cudaError_t e, const char *where);
 
+// a1: validates one pixel and derives its row shift l = ceil(q) mod N
+// (Theorem 2; q = fmod(t_d, t_r) N / t_r in IEEE FP64) into d.  SPL_EINVAL
+// for an invalid pixel.  Every entry point takes its pixels through here.
+spl_status_t make_pixel(const spl_pixel_t &p, PixelDev &d);
+
 // Device-resident state of one chain's iteration (single-pixel API).
 struct ChainState {
     StopState st;
@@ -108,6 +113,13 @@ cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s);
 // status[1]: CTAs that left the grid barrier on the abort; err_flag set by the
 // CTA that gave up).  bar: chain_run_bar_words() zeroed words.
 cudaError_t launch_selftest_waits(unsigned *bar, int *err_flag, int *status, cudaStream_t s);
+
+// FP32 FMA throughput kernel on `sms` SMs: fma_peak_flop() FLOP per launch,
+// fma_peak_out_floats() floats written to out.
+int fma_peak_blocks(int sms);
+double fma_peak_flop(int sms, int iters);
+size_t fma_peak_out_floats(int sms);
+cudaError_t launch_fma_peak(float *out, int sms, int iters, cudaStream_t s);
 
 struct FinishArgs {
     int mode;                // 0 materialised (GEMV partials), 1 fused (split partials)

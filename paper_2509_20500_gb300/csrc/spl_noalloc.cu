@@ -6,8 +6,9 @@
 // inside a host application whose own allocator owns the GPU memory budget.
 // This entry point serves them.  It runs the same persistent batch kernel as
 // spl_batch_stationary, but every piece of device scratch the kernel needs
-// (work list, work-queue counter, per-pixel reports) lives in one
-// file-scope __device__ array of fixed size, and the host-side staging lives
+// (work list, work-queue counter, per-pixel reports, per-pixel flux
+// constants) lives in one file-scope __device__ array of fixed size (about
+// 15.2 MB), and the host-side staging lives
 // in static host arrays.  It calls no cudaMalloc, cudaFree, cudaMallocHost
 // or any other allocating routine.
 //
@@ -17,7 +18,11 @@
 // needed).  Larger requests return SPL_EINVAL.
 //
 // Every GPU that loads this library holds the array until the process
-// exits.  All calls share it and it keeps the previous call's contents;
+// exits.  With lazy module loading (the CUDA default) the array is reserved
+// when this file's module is first loaded on a device, which the first
+// call's cudaGetSymbolAddress does: that first call may therefore reserve
+// memory and synchronise the device, so make it during start-up, before any
+// stream capture.  All calls share it and it keeps the previous call's contents;
 // what must start at zero (the work-queue counter) is cleared by each call.
 // Two calls whose work overlaps on the GPU (for example on two streams)
 // race on the array; issue them one after the other.
@@ -42,8 +47,10 @@ constexpr size_t kWorkBytes = sizeof(PixelDev) * kNoAllocMaxPixels;
 constexpr size_t kReportBytes = sizeof(ReportDev) * kNoAllocMaxPixels;
 constexpr size_t kConstBytes = sizeof(PixelConst) * kNoAllocMaxPixels;
 constexpr size_t kScratchBytes = kCounterBytes + kWorkBytes + kReportBytes + kConstBytes;
+static_assert(kScratchBytes == 15204608, "scratch size stated in the header");
 
-// The scratch array (about 13 MB).  Host code must not use its name as an
+// The scratch array: 256 B counter + 64 B x 65536 work list + 24 B x 65536
+// reports + 144 B x 65536 per-pixel constants = 15,204,608 bytes.  Host code must not use its name as an
 // address: it is a host-side stand-in.  The device address comes from
 // cudaGetSymbolAddress, per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -68,39 +75,6 @@ spl_status_t scratch_ptr(unsigned char **out) {
         g_dev_scratch[dev] = p;
     }
     *out = static_cast<unsigned char *>(g_dev_scratch[dev]);
-    return SPL_OK;
-}
-
-// Same validation and shift rule as the allocating entry points.
-spl_status_t make_pixel_na(const spl_pixel_t &p, PixelDev &d) {
-    if (!(std::isfinite(p.t_r) && std::isfinite(p.t_d) && std::isfinite(p.tau) && std::isfinite(p.sigma) &&
-          std::isfinite(p.S) && std::isfinite(p.B)))
-        return SPL_EINVAL;
-    if (p.n_bins < 2 || p.n_bins > kNoAllocMaxBins) return SPL_EINVAL;
-    if (!(p.t_r > 0.0) || !(p.sigma > 0.0) || p.t_d < 0.0 || p.S < 0.0 || p.B < 0.0) return SPL_EINVAL;
-    if (!(p.S + p.B > 0.0) || p.S + p.B > 120.0) return SPL_EINVAL;
-    if (p.tau < 0.0 || p.tau >= p.t_r || p.shift_override < -1) return SPL_EINVAL;
-    const int32_t N = p.n_bins;
-    int64_t l;
-    if (p.shift_override >= 0) {
-        l = p.shift_override;
-    } else {
-        const volatile double x_d = std::fmod(p.t_d, p.t_r);
-        const volatile double num = x_d * (double)N;
-        l = (int64_t)std::ceil(num / p.t_r);
-    }
-    l %= N;
-    if (l < 0) l += N;
-    d.t_r = p.t_r;
-    d.tau = p.tau;
-    d.sigma = p.sigma;
-    d.S = p.S;
-    d.B = p.B;
-    d.N = N;
-    d.l = (int32_t)l;
-    d.out_off = 0;
-    d.index = 0;
-    d.pad_ = 0;
     return SPL_OK;
 }
 
@@ -150,7 +124,7 @@ extern "C" spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels
     }
     for (int32_t k = 0; k < n; ++k) {
         PixelDev d;
-        st = make_pixel_na(h_pixels[k], d);
+        st = make_pixel(h_pixels[k], d);   // validation and row shift of every entry point
         if (st != SPL_OK) return st;
         d.index = k;
         g_host_work[g_count_by_n[d.N]++] = d;

@@ -57,7 +57,8 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_mlp_get_params", "spl_mlp_get_state", "spl_mlp_set_state", "spl_mlp_forward", "spl_mlp_loss_grad", "spl_mlp_train_step", "spl_mlp_logits",
             "spl_mlp_free", "spl_batch_stationary_learned",
             "spl_batch_stationary_learned_host", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
-            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup"]
+            "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup",
+            "spl_fp32_fma_peak"]
 
 _lib = None
 _lock = threading.Lock()
@@ -165,6 +166,8 @@ def lib():
         L.spl_chain_run_plan.restype = ctypes.c_int
         L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         L.spl_gemm_bf16.restype = ctypes.c_int
+        L.spl_fp32_fma_peak.argtypes = [i32, i32, vp, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(i32)]
+        L.spl_fp32_fma_peak.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -312,7 +315,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
 
 
 def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,
-                             offsets=None, reports: bool = True, stream=None):
+                             offsets=None, reports: bool = True, stream=None, c_pixels=None):
     """spl_batch_stationary_noalloc: the batch solver for callers that may not
     allocate device memory (its scratch is a fixed device array inside the
     library).  ``out`` and ``offsets`` are caller-owned device tensors; they
@@ -325,7 +328,7 @@ def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 
         offsets = torch.from_numpy(off).to("cuda")
     if out is None:
         out = torch.empty(max(1, int(off[-1])), dtype=torch.float32, device="cuda")
-    arr = pixels_to_c(px)
+    arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
     st = lib().spl_batch_stationary_noalloc(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out),
                                             _dptr(offsets), reps, _stream_ptr(stream))
@@ -388,6 +391,15 @@ def selftest_bounded_waits(stream=None) -> int:
     """spl_selftest_bounded_waits: the status (SPL_OK when every wait gave up
     as designed)."""
     return int(lib().spl_selftest_bounded_waits(_stream_ptr(stream)))
+
+
+def fp32_fma_peak(iters: int = 800_000, reps: int = 5, stream=None) -> dict:
+    """spl_fp32_fma_peak: measured FP32 FMA throughput (TFLOP/s, median and
+    fastest of `reps` launches) and the SM count."""
+    med, best, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().spl_fp32_fma_peak(int(iters), int(reps), _stream_ptr(stream), ctypes.byref(med), ctypes.byref(best),
+                                   ctypes.byref(sms)), "spl_fp32_fma_peak")
+    return {"tflops_median": med.value, "tflops_best": best.value, "sms": int(sms.value)}
 
 
 def batch_kernel_ms() -> float:
