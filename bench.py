@@ -598,6 +598,31 @@ def run_gpu(args):
             for key in ("materialized", "fused"):
                 hr["sweep"][key + "_max_l1"] = max(r[key + "_l1"] for r in sweep)
                 hr["sweep"][key + "_max_abs"] = max(r[key + "_max_abs"] for r in sweep)
+        # the 12 sweep pixels in one multi-chain launch (one CTA group per
+        # chain): device time of the whole call (start kernel, cooperative
+        # launch, result copy) by CUDA events, L2 flushed between calls
+        cs = spl.ChainSet(hx)
+        mo, moff, mreps = cs.stationary(tol=TOL)
+        assert np.all(mreps["status"] == 0)
+        for _ in range(3):
+            cs.stationary(tol=TOL, reports=False)
+        mms, _ = timed_steps(lambda: cs.stationary(tol=TOL, out=mo, reports=False), 10, flush, stream)
+        m_ms = statistics.median(mms)
+        mflop = float(np.sum(2.0 * hx["n_bins"].astype(np.float64) ** 2 * mreps["iters"]))
+        mt = mflop / (m_ms / 1e3) / 1e12
+        multi = {"value": len(hx) / (m_ms / 1e3), "unit": "PDFs/s", "ms_per_call": m_ms,
+                 "iters": mreps["iters"].tolist(),
+                 "roofline": {"bound": "alu", "achieved": mt, "peak": peak, "unit": "TFLOP/s", "frac": mt / peak,
+                              "work": "2 FLOP x N^2 per power step that the stop rule counts (iters), summed"},
+                 "step_balance": float(mreps["iters"].mean() / mreps["iters"].max()),
+                 "what": "spl_chains_stationary: 12 fused chains, one cooperative launch, ~25 CTAs per chain"}
+        if hrefs is not None:
+            mo_h = mo.cpu().numpy().astype(np.float64)
+            dd = [np.abs(mo_h[moff[k]:moff[k + 1]] - hrefs[k]) for k in range(len(hx))]
+            multi["max_l1"] = max(float(d.sum()) for d in dd)
+            multi["max_abs"] = max(float(d.max()) for d in dd)
+        cs.close()
+        hr["sweep"]["multi_chain_launch"] = multi
         extra["highres_n10000"] = hr
 
     # end to end through the public API: pixel list from host memory (copied

@@ -341,6 +341,29 @@ SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_p
                                                        spl_report_t *h_reports, void *stream,
                                                        const spl_batch_opts_t *opts /* nullable */);
 
+/*
+ * Stationary pmfs of several fused chains in one launch (Sec. 3.4, the
+ * matrix-free power iteration of Eq. 6, as spl_stationary with a uniform
+ * start, for many pixels at once).
+ *   chains: n distinct chains built with SPL_FUSED on one and the same stream
+ *   (the call runs on that stream).  One cooperative launch (at most 32
+ *   chains per launch; more run as consecutive launches) splits the resident
+ *   CTAs into one group per chain, sized in proportion to N^2; each group
+ *   runs every power step of its chain with its own barrier and stop rule, so
+ *   one chain's dependent round trips overlap the others' FMA work.
+ *   d_out: device [sum of n_bins] FP32, the pmfs packed in chain order.
+ *   h_reports: NULL or host [n]; with it the call synchronises the stream and
+ *   returns the worst per-chain status, without it the call is asynchronous.
+ *   Each chain's pmf is the one spl_stationary gives (same steps, same stop
+ *   rule; the column pass is partitioned over fewer CTAs, so sums are added
+ *   in another order).
+ * Errors: SPL_EINVAL (NULL chain, a materialised chain, a chain given twice,
+ * chains on different streams, n < 0, tol <= 0, max_iter < 1), SPL_ENOMEM,
+ * SPL_ECUDA; per chain SPL_ENOCONV, SPL_ETIMEOUT as spl_stationary.
+ */
+SPL_API spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_t n, double tol, int32_t max_iter,
+                                           float *d_out, spl_report_t *h_reports);
+
 /* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
  * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a
  * chain of n_bins bins runs on `grid` CTAs; its column pass is cut into

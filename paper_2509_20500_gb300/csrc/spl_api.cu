@@ -156,6 +156,7 @@ struct spl_chain {
           *run_blk = nullptr;
     int *run_ticket = nullptr;
     unsigned *run_bar = nullptr;
+    size_t run_part_cap = 0;         // floats of run_part
     // kGraphSteps power steps captured once as a CUDA graph, replayed per chunk
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t steps_exec = nullptr;
@@ -218,6 +219,18 @@ static void plan_split(spl_chain *c) {
     c->ld_part = c->vlen;
 }
 
+// Units [b U / G, (b+1) U / G) of CTA b: the partial slots one CTA needs
+// (tiles its range touches) and the largest range.
+static void run_partition(long long U, int RB, int G, int *segs, long long *umax) {
+    *segs = 1;
+    *umax = 0;
+    for (int b = 0; b < G; ++b) {
+        const long long u0 = (long long)b * U / G, u1 = (long long)(b + 1) * U / G;
+        *segs = std::max(*segs, (int)((u1 - 1) / RB - u0 / RB) + 1);
+        *umax = std::max(*umax, u1 - u0);
+    }
+}
+
 // Plan of the persistent fused iteration (host arithmetic only): as many CTAs
 // as stay resident (at most one per work unit), the work units (128-column
 // tile x 32-row block) split evenly over them, the partial slots one CTA
@@ -231,11 +244,7 @@ extern "C" spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t 
     const int G = (int)std::min<long long>(std::min((long long)blocks_per_sm * sms, (long long)chain_run_max_grid()), U);
     int segs = 1;
     long long umax = 0;
-    for (int b = 0; b < G; ++b) {
-        const long long u0 = (long long)b * U / G, u1 = (long long)(b + 1) * U / G;
-        segs = std::max(segs, (int)((u1 - 1) / RB - u0 / RB) + 1);
-        umax = std::max(umax, u1 - u0);
-    }
+    run_partition(U, RB, G, &segs, &umax);
     out->grid = G;
     out->tiles = T;
     out->row_blocks = RB;
@@ -262,7 +271,8 @@ static spl_status_t plan_run(spl_chain *c) {
     SPL_CU(cudaMemset(c->run_vb, 0, 2 * sizeof(float) * c->vlen));
     SPL_CU(dalloc(&c->run_pi, (size_t)c->N));
     SPL_CU(dalloc(&c->run_tsum, 2 * (size_t)T));
-    SPL_CU(dalloc(&c->run_part, (size_t)G * pl.segs * chain_run_tile_cols()));
+    c->run_part_cap = (size_t)G * pl.segs * chain_run_tile_cols();
+    SPL_CU(dalloc(&c->run_part, c->run_part_cap));
     SPL_CU(dalloc(&c->run_blk, 2 * (size_t)G * 4));
     SPL_CU(dalloc(&c->run_ticket, (size_t)T));
     SPL_CU(dalloc(&c->run_bar, (size_t)chain_run_bar_words()));
@@ -1167,6 +1177,114 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     SPL_CU(cudaStreamSynchronize(s));
     return SPL_OK;
+}
+
+// Group sizes of a multi-chain launch: `total` resident CTAs shared in
+// proportion to each chain's work per pass (N^2), at least one each, at most
+// one per work unit and at most the chain's own grid; the CTAs left over go
+// one at a time to the chain with the most work per CTA.
+static void multi_groups(spl_chain *const *cs, int m, int total, int *G) {
+    double W = 0.0;
+    for (int g = 0; g < m; ++g) W += (double)cs[g]->N * cs[g]->N;
+    int used = 0;
+    std::vector<int> cap((size_t)m);
+    for (int g = 0; g < m; ++g) {
+        const long long U = (long long)cs[g]->run_T * cs[g]->run_RB;
+        cap[g] = (int)std::min<long long>(std::min<long long>(U, cs[g]->run_grid), chain_run_max_grid());
+        const double share = (double)total * cs[g]->N * (double)cs[g]->N / W;
+        G[g] = std::max(1, std::min(cap[g], (int)share));
+        used += G[g];
+    }
+    while (used < total) {
+        int best = -1;
+        double best_w = 0.0;
+        for (int g = 0; g < m; ++g) {
+            if (G[g] >= cap[g]) continue;
+            const double w = (double)cs[g]->N * cs[g]->N / G[g];
+            if (w > best_w) { best_w = w; best = g; }
+        }
+        if (best < 0) break;
+        ++G[best];
+        ++used;
+    }
+}
+
+extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_t n, double tol, int32_t max_iter,
+                                              float *d_out, spl_report_t *h_reports) {
+    if (n < 0 || (n > 0 && (!chains || !d_out)) || !(tol > 0.0) || max_iter < 1) return SPL_EINVAL;
+    if (n == 0) return SPL_OK;
+    for (int32_t k = 0; k < n; ++k)
+        if (!chains[k] || chains[k]->mode != SPL_FUSED || chains[k]->stream != chains[0]->stream) return SPL_EINVAL;
+    for (int32_t k = 0; k < n; ++k)
+        for (int32_t j = 0; j < k; ++j)
+            if (chains[j] == chains[k]) return SPL_EINVAL;   // one chain's buffers cannot serve two groups
+    BatchWorkspace *ws = nullptr;
+    spl_status_t st = ws_get(&ws);
+    if (st != SPL_OK) return st;
+    std::lock_guard<std::mutex> lock(ws->mu);
+    cudaStream_t s = chains[0]->stream;
+    cudaError_t e = grow(&ws->reps, &ws->reps_cap, (size_t)n);
+    if (e != cudaSuccess) return status_of_alloc(e, "reports");
+    const int bps = std::min(2, chain_multi_blocks_per_sm(chain_run_max_chunk()));
+    if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "multi-chain occupancy");
+    const int total = bps * num_sms_current();
+    const int per_launch = std::min(kChainMultiMax, total);
+    static_assert(sizeof(ChainMultiArgs) < 30000, "kernel parameter size");
+    ChainMultiArgs M;
+    int64_t off = 0;
+    for (int32_t k0 = 0; k0 < n; k0 += per_launch) {
+        const int m = std::min<int32_t>(per_launch, n - k0);
+        std::memset(&M, 0, sizeof(M));
+        M.n = m;
+        int G[kChainMultiMax];
+        multi_groups(chains + k0, m, total, G);
+        int chunk = 0;
+        M.begin[0] = 0;
+        for (int g = 0; g < m; ++g) {
+            spl_chain *c = chains[k0 + g];
+            const long long U = (long long)c->run_T * c->run_RB;
+            int segs = 1;
+            long long umax = 0;
+            run_partition(U, c->run_RB, G[g], &segs, &umax);
+            const size_t need = (size_t)G[g] * segs * chain_run_tile_cols();
+            if (need > c->run_part_cap) {
+                // a smaller group covers more tiles per CTA: more partial slots
+                float *np = nullptr;
+                if ((e = dalloc(&np, need)) != cudaSuccess) return status_of_alloc(e, "chain partials");
+                SPL_CU(cudaStreamSynchronize(c->stream));
+                cudaFree(c->run_part);
+                c->run_part = np;
+                c->run_part_cap = need;
+            }
+            ChainRunArgs a = run_args(c);
+            a.segs = segs;
+            a.chunk = (int)std::min<long long>(chain_run_max_chunk(), umax * 32);
+            chunk = std::max(chunk, a.chunk);
+            M.c[g] = a;
+            M.off[g] = off;
+            off += c->N;
+            M.begin[g + 1] = M.begin[g] + G[g];
+        }
+        SPL_CU(launch_chain_multi(M, M.begin[m], chunk, (float)(0.5 * tol), max_iter, d_out, ws->reps + k0, s));
+    }
+    if (!h_reports) return SPL_OK;
+    e = grow_host(&ws->h_reps, &ws->h_reps_cap, (size_t)n);
+    if (e != cudaSuccess) return status_of_alloc(e, "pinned reports");
+    SPL_CU(cudaMemcpyAsync(ws->h_reps, ws->reps, sizeof(ReportDev) * n, cudaMemcpyDeviceToHost, s));
+    SPL_CU(cudaStreamSynchronize(s));
+    spl_status_t worst = SPL_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        const ReportDev &r = ws->h_reps[k];
+        spl_report_t &o = h_reports[k];
+        o.iters = r.iters;
+        o.status = r.status;
+        o.last_step_l1 = r.last_step_l1;
+        o.err_bound = r.err_bound;
+        o.lambda2_abs = r.lambda2_abs;
+        o.lambda2_phase = r.lambda2_phase;
+        if (r.status > (int)worst) worst = (spl_status_t)r.status;
+    }
+    return worst;
 }
 
 extern "C" spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol,

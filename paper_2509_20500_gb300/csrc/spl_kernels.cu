@@ -1268,19 +1268,20 @@ __device__ __forceinline__ int add_acq_rel_gpu(int *p, int v) {
     return old;
 }
 
-// Grid-wide barrier over a cooperative launch.  bar[0] counts arrivals since
-// launch, bar[kBarGen] (another 128-byte line) is the released generation;
-// gen is the calling CTA's count of barriers passed (thread 0's copy is the
-// one used).  False if the grid was aborted.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag,
-                                          uint32_t limit = kGridSpinLimit) {
+// Barrier over the G CTAs of one group of a cooperative launch (the whole
+// grid, or the CTAs that share one chain); b is the CTA's index in its group.
+// bar[0] counts arrivals since launch, bar[kBarGen] (another 128-byte line)
+// is the released generation; gen is the calling CTA's count of barriers
+// passed (thread 0's copy is the one used).  False if the group was aborted.
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag, int b,
+                                          int G, uint32_t limit = kGridSpinLimit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
         const unsigned next = gen + 1u;
         red_release_add_gpu(&bar[0], 1u);
-        if (blockIdx.x == 0) {
-            const unsigned target = next * gridDim.x;
+        if (b == 0) {
+            const unsigned target = next * (unsigned)G;
             uint32_t spins = 0;
             while ((int)(ld_acquire_gpu(&bar[0]) - target) < 0) {
                 if (++spins > limit) {
@@ -1378,14 +1379,15 @@ __device__ __forceinline__ void run_tile_reduce(const ChainRunArgs &a, int t, lo
     if (tid == 0) tdst[t] = tsb;
 }
 
-__global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
+// Every power step of one chain on the G CTAs of its group; b is this CTA's
+// index in the group.
+__device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int b, const int G) {
     extern __shared__ float4 smem4[];
     float *sv = reinterpret_cast<float *>(smem4);
     __shared__ float wred[kRunW][kRunTW];
     __shared__ float red[5 * kRunW + 5];
     __shared__ int s_flag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x;
     const int N = a.N, T = a.T, RB = a.RB;
     const size_t vlen = (size_t)a.vlen;
     const long long U = (long long)T * RB;
@@ -1493,7 +1495,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
             __syncthreads();   // red is reused
             run_tile_reduce(a, t_last, U, G, ydst, vdst, tdst, red);
         }
-        if (!grid_sync(a.bar, gen, a.err_flag, &s_flag)) {
+        if (!grid_sync(a.bar, gen, a.err_flag, &s_flag, b, G)) {
             if (b == 0) {
                 stp->st = st;
                 stp->done = 1;
@@ -1574,6 +1576,76 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
+    chain_run_body(a, blockIdx.x, gridDim.x);
+}
+
+// Several chains in one cooperative launch: chain g runs on CTAs
+// [begin[g], begin[g+1]) with its own barrier, tickets and stop rule, so one
+// chain's dependent L2 round trips (staging, tickets, barrier, normalisation)
+// overlap the other chains' FMA loops.  The groups never wait on one another.
+__global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_constant__ ChainMultiArgs m) {
+    int g = 0;
+    while (g + 1 < m.n && (int)blockIdx.x >= m.begin[g + 1]) ++g;
+    chain_run_body(m.c[g], (int)blockIdx.x - m.begin[g], m.begin[g + 1] - m.begin[g]);
+}
+
+// Start of a multi-chain iteration, one block per chain: uniform pi^(0) (as
+// init_iter_kernel without a warm start), cleared step vectors, the first
+// broadcast vector h_k = pi^(0)_{(k-l) mod N} rho_k, the stop state, and the
+// chain's error flag, tile tickets and barrier words zeroed.
+__global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_constant__ ChainMultiArgs m,
+                                                                  float tol_err, int max_iter) {
+    const ChainRunArgs &a = m.c[blockIdx.x];
+    const int N = a.N, tid = threadIdx.x;
+    const float p0 = 1.f / (float)N;
+    for (int j = tid; j < N; j += kRunNT) {
+        a.pi[j] = p0;
+        a.d1[j] = 0.f;
+        a.d2[j] = 0.f;
+    }
+    for (int k = tid; k < a.vlen; k += kRunNT) {
+        float *v0 = const_cast<float *>(a.v0);
+        v0[k] = k < N ? p0 * a.rho[k] : 0.f;
+    }
+    for (int t = tid; t < a.T; t += kRunNT) a.tile_ticket[t] = 0;
+    for (int q = tid; q < 2 * kBarGen; q += kRunNT) a.bar[q] = 0u;
+    if (tid == 0) {
+        *a.err_flag = 0;
+        ChainState *stp = a.state;
+        StopState st;
+        stop_init(st, 1.f, 0.f);
+        stp->st = st;
+        stp->done = 0;
+        stp->status = ST_ENOCONV;
+        stp->tol_err = tol_err;
+        stp->max_iter = max_iter;
+        stp->min_iter = 1;
+    }
+}
+
+// End of a multi-chain iteration, one block per chain: the result copied to
+// out + off[g] and the chain's report (as the single-chain call reports it).
+__global__ void __launch_bounds__(kRunNT) chain_multi_finish_kernel(const __grid_constant__ ChainMultiArgs m,
+                                                                    float *__restrict__ out,
+                                                                    ReportDev *__restrict__ reps) {
+    const ChainRunArgs &a = m.c[blockIdx.x];
+    float *dst = out + m.off[blockIdx.x];
+    for (int j = threadIdx.x; j < a.N; j += kRunNT) dst[j] = a.pi[j];
+    if (threadIdx.x == 0 && reps) {
+        const ChainState &h = *a.state;
+        const int err = *a.err_flag;
+        ReportDev r;
+        r.iters = h.st.k;
+        r.status = err ? ST_ETIMEOUT : (h.done && h.status == ST_OK ? ST_OK : ST_ENOCONV);
+        r.last_step_l1 = h.st.k > 0 ? h.st.delta[(h.st.k - 1) & 7] : 0.f;
+        r.err_bound = h.st.err;
+        r.lambda2_abs = h.st.rho;
+        r.lambda2_phase = h.st.theta;
+        reps[blockIdx.x] = r;
+    }
+}
+
 // ======================================================================
 // Self-test of the bounded waits
 // ======================================================================
@@ -1597,7 +1669,7 @@ __global__ void selftest_grid_kernel(unsigned *bar, int *err_flag, int *status, 
     __shared__ int s_flag;
     unsigned gen = 0u;
     if (blockIdx.x == gridDim.x - 1) return;             // this CTA never arrives
-    const bool ok = grid_sync(bar, gen, err_flag, &s_flag, limit);
+    const bool ok = grid_sync(bar, gen, err_flag, &s_flag, blockIdx.x, gridDim.x, limit);
     if (threadIdx.x == 0 && !ok) atomicAdd(status + 1, 1);
 }
 
@@ -2014,6 +2086,32 @@ cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s) {
     void *params[] = {&args};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(chain_run_kernel), dim3(grid), dim3(kRunNT),
                                        params, smem, s);
+}
+
+cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, int chunk, float tol_err, int max_iter,
+                               float *out, ReportDev *reps, cudaStream_t s) {
+    chain_multi_init_kernel<<<m.n, kRunNT, 0, s>>>(m, tol_err, max_iter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = chain_run_smem_bytes(chunk);
+    e = cudaFuncSetAttribute(chain_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *params[] = {const_cast<ChainMultiArgs *>(&m)};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(chain_multi_kernel), dim3(grid), dim3(kRunNT),
+                                    params, smem, s);
+    if (e != cudaSuccess) return e;
+    chain_multi_finish_kernel<<<m.n, kRunNT, 0, s>>>(m, out, reps);
+    return cudaGetLastError();
+}
+
+int chain_multi_blocks_per_sm(int chunk) {
+    const size_t smem = chain_run_smem_bytes(chunk);
+    if (cudaFuncSetAttribute(chain_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chain_multi_kernel, kRunNT, smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 size_t finish_blk_floats(int vlen) { return 5 * (size_t)((vlen + kFinishNT - 1) / kFinishNT); }

@@ -101,6 +101,18 @@ struct ChainRunArgs {
     int *err_flag;           // set if a CTA gave up waiting at the barrier
 };
 
+// Several fused chains in one cooperative launch (at most kChainMultiMax):
+// chain g runs on CTAs [begin[g], begin[g+1]) with the partition of its
+// column pass planned for that group size (c[g].segs, c[g].chunk), and its
+// result goes to out + off[g].
+constexpr int kChainMultiMax = 32;
+struct ChainMultiArgs {
+    ChainRunArgs c[kChainMultiMax];
+    int64_t off[kChainMultiMax];
+    int begin[kChainMultiMax + 1];
+    int n;
+};
+
 int chain_run_tile_cols();
 int chain_run_bar_words();
 int chain_run_max_grid();
@@ -109,6 +121,13 @@ size_t chain_run_smem_bytes(int chunk);
 // CTAs per SM the cooperative launch can keep resident (0 on error).
 int chain_run_blocks_per_sm(int chunk);
 cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s);
+// Multi-chain iteration: init kernel (uniform start, stop state tol_err /
+// max_iter, cleared tickets, barrier and error flag), the cooperative launch
+// of `grid` CTAs with `chunk` rows of shared staging, and the finish kernel
+// (results to out, reports to reps if not NULL).
+cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, int chunk, float tol_err, int max_iter,
+                               float *out, ReportDev *reps, cudaStream_t s);
+int chain_multi_blocks_per_sm(int chunk);
 // Waits that run out on purpose (status[0]: the mbarrier wait gave up;
 // status[1]: CTAs that left the grid barrier on the abort; err_flag set by the
 // CTA that gave up).  bar: chain_run_bar_words() zeroed words.

@@ -58,7 +58,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_mlp_free", "spl_batch_stationary_learned",
             "spl_batch_stationary_learned_host", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup",
-            "spl_fp32_fma_peak"]
+            "spl_fp32_fma_peak", "spl_chains_stationary"]
 
 _lib = None
 _lock = threading.Lock()
@@ -166,6 +166,8 @@ def lib():
         L.spl_chain_run_plan.restype = ctypes.c_int
         L.spl_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         L.spl_gemm_bf16.restype = ctypes.c_int
+        L.spl_chains_stationary.argtypes = [vp, i32, f64, i32, vp, ctypes.POINTER(spl_report_t)]
+        L.spl_chains_stationary.restype = ctypes.c_int
         L.spl_fp32_fma_peak.argtypes = [i32, i32, vp, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(i32)]
         L.spl_fp32_fma_peak.restype = ctypes.c_int
         _lib = L
@@ -288,6 +290,44 @@ class Chain:
             self.close()
         except Exception:
             pass
+
+
+class ChainSet:
+    """Fused chains of several pixels, solved together by
+    spl_chains_stationary (one cooperative launch, one CTA group per chain)."""
+
+    def __init__(self, px: np.ndarray, stream=None):
+        px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
+        self.chains = [Chain(px[k:k + 1], SPL_FUSED, stream) for k in range(len(px))]
+        self.off = offsets_of(px)
+        self._arr = (ctypes.c_void_p * max(1, len(self.chains)))(*[c._c.value for c in self.chains])
+
+    def stationary(self, tol: float = 1e-6, max_iter: int = 1000, out=None, reports: bool = True):
+        import torch
+        n = len(self.chains)
+        if out is None:
+            out = torch.empty(max(1, int(self.off[-1])), dtype=torch.float32, device="cuda")
+        reps = (spl_report_t * max(1, n))() if reports else None
+        st = lib().spl_chains_stationary(self._arr, n, float(tol), int(max_iter), _dptr(out), reps)
+        _check(st, "spl_chains_stationary", (SPL_OK, SPL_ENOCONV))
+        return out, self.off, (_reports_np(ctypes.addressof(reps), n) if reports else None)
+
+    def close(self):
+        for c in self.chains:
+            c.close()
+        self.chains = []
+
+
+def chains_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, stream=None):
+    """Builds fused chains for the pixels and solves them in one launch;
+    returns (packed pmfs, offsets, reports)."""
+    cs = ChainSet(px, stream)
+    try:
+        return cs.stationary(tol=tol, max_iter=max_iter)
+    finally:
+        import torch
+        torch.cuda.current_stream().synchronize()
+        cs.close()
 
 
 def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, warm=None, out=None,

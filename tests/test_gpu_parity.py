@@ -189,6 +189,67 @@ def test_highres_materialized_and_fused(spl, highres_refs, k):
         ch.close()
 
 
+def test_chains_multi_launch_sweep_vs_oracle(spl, highres_refs):
+    """The 12 sweep pixels solved together (spl_chains_stationary: one
+    cooperative launch, one CTA group of about 25 CTAs per chain): every pmf
+    within the tolerance of the oracle, the same step counts as the chain
+    solved alone within one step, and a second call gives the same pmfs bit
+    for bit (groups add their partials in a fixed order)."""
+    px, refs = highres_refs
+    cs = spl.ChainSet(px)
+    out, off, reps = cs.stationary(tol=1e-6, max_iter=500)
+    o = out.cpu().numpy()
+    assert np.all(reps["status"] == 0), reps
+    for k in range(len(px)):
+        _assert_pmf(o[off[k]:off[k + 1]], refs[k], (k, reps[k]))
+    out2, _, reps2 = cs.stationary(tol=1e-6, max_iter=500)
+    np.testing.assert_array_equal(out2.cpu().numpy(), o)
+    np.testing.assert_array_equal(reps2["iters"], reps["iters"])
+    for k in (0, 5, 11):
+        ch = spl.Chain(px[k:k + 1], spl.SPL_FUSED)
+        _, r1 = ch.stationary(tol=1e-6, max_iter=500)
+        assert abs(int(r1["iters"]) - int(reps["iters"][k])) <= 1
+        ch.close()
+    cs.close()
+
+
+def test_chains_multi_launch_mixed_sizes_and_many_chains(spl):
+    """Ragged sizes in one launch (N = 2 ... 18000; the large chain's group
+    stages several shared-memory windows per CTA) and more chains than one
+    launch takes (40 > 32: two consecutive launches), each against the
+    reparameterised oracle with the same shift."""
+    mixed = np.concatenate([W.pixel(18000, 130.0, 30.0, 0.3, 0.5, 0.5), W.pixel(2, 10.0, 30.0, 3.0, 1.0, 1.0),
+                            W.pixel(37, 75.0, 30.0, 2.0, 0.5, 0.5), W.pixel(333, 130.0, 50.0, 1.0, 3.0, 6.0),
+                            W.pixel(2000, 75.0, 5.0, 1.0, 5.0, 0.01), W.pixel(1024, 95.0, 30.0, 0.5, 9.0, 9.0)])
+    many = W.random_small(40, seed=61, n_min=2, n_max=700)
+    for px in (mixed, many):
+        out, off, reps = spl.chains_stationary(px, tol=1e-6, max_iter=1000)
+        o = out.cpu().numpy()
+        assert np.all(reps["status"] == 0), reps
+        pix = W.as_dicts(px)
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(4) as ex:
+            refs = list(ex.map(lambda p: oracle.stationary(p, shift=oracle.shift_l(p)), pix))
+        for k, ref in enumerate(refs):
+            _assert_pmf(o[off[k]:off[k + 1]], ref, (k, pix[k]["n_bins"], reps[k]))
+
+
+def test_chains_multi_launch_rejects_bad_sets(spl):
+    import ctypes
+    L = spl.lib()
+    a = spl.Chain(W.pixel(300, 75.0, 30.0, 0.5, 0.5, 0.5), spl.SPL_FUSED)
+    m = spl.Chain(W.pixel(300, 75.0, 30.0, 0.5, 0.5, 0.5), spl.SPL_MATERIALIZED)
+    out = torch.empty(600, dtype=torch.float32, device="cuda")
+    for pair in ((a, a), (a, m)):
+        arr = (ctypes.c_void_p * 2)(pair[0]._c.value, pair[1]._c.value)
+        assert L.spl_chains_stationary(arr, 2, 1e-6, 100, ctypes.c_void_p(out.data_ptr()), None) == spl.SPL_EINVAL
+    arr = (ctypes.c_void_p * 1)(a._c.value)
+    assert L.spl_chains_stationary(arr, 1, 0.0, 100, ctypes.c_void_p(out.data_ptr()), None) == spl.SPL_EINVAL
+    assert L.spl_chains_stationary(arr, 0, 1e-6, 100, None, None) == spl.SPL_OK
+    a.close()
+    m.close()
+
+
 def test_chain_timing_leaves_chain_usable_and_results_repeat(spl):
     """The finish stages add their per-CTA partials in CTA order whichever
     CTA arrives last: a chain gives the same pmf bit for bit on every call,
