@@ -364,6 +364,16 @@ SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_p
 SPL_API spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_t n, double tol, int32_t max_iter,
                                            float *d_out, spl_report_t *h_reports);
 
+/* Group sizes of one multi-chain launch (host arithmetic only, no GPU
+ * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident,
+ * groups[g] gets the CTAs of chain g (n_bins[g] bins): shares of
+ * sms x blocks_per_sm in proportion to n_bins^2, at least 1, at most the
+ * chain's own grid (spl_chain_run_plan), the remainder to the chain with the
+ * most work per CTA.  1 <= n <= 32 and n <= sms x blocks_per_sm, else
+ * SPL_EINVAL. */
+SPL_API spl_status_t spl_chains_plan(const int32_t *n_bins, int32_t n, int32_t sms, int32_t blocks_per_sm,
+                                     int32_t *groups);
+
 /* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
  * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a
  * chain of n_bins bins runs on `grid` CTAs; its column pass is cut into

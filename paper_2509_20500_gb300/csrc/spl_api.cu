@@ -1181,32 +1181,54 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
 
 // Group sizes of a multi-chain launch: `total` resident CTAs shared in
 // proportion to each chain's work per pass (N^2), at least one each, at most
-// one per work unit and at most the chain's own grid; the CTAs left over go
-// one at a time to the chain with the most work per CTA.
-static void multi_groups(spl_chain *const *cs, int m, int total, int *G) {
+// cap[g] each (the chain's own grid: at most one CTA per work unit); the CTAs
+// left over go one at a time to the chain with the most work per CTA.  With
+// m <= total every chain keeps at least one CTA and the sum never exceeds
+// total.
+static void multi_groups(const int32_t *N, const int32_t *cap, int m, int total, int32_t *G) {
     double W = 0.0;
-    for (int g = 0; g < m; ++g) W += (double)cs[g]->N * cs[g]->N;
+    for (int g = 0; g < m; ++g) W += (double)N[g] * N[g];
+    auto work = [&](int g) { return (double)N[g] * N[g] / G[g]; };
     int used = 0;
-    std::vector<int> cap((size_t)m);
     for (int g = 0; g < m; ++g) {
-        const long long U = (long long)cs[g]->run_T * cs[g]->run_RB;
-        cap[g] = (int)std::min<long long>(std::min<long long>(U, cs[g]->run_grid), chain_run_max_grid());
-        const double share = (double)total * cs[g]->N * (double)cs[g]->N / W;
+        const double share = (double)total * N[g] * (double)N[g] / W;
         G[g] = std::max(1, std::min(cap[g], (int)share));
         used += G[g];
     }
+    // the floor of one CTA per chain may overshoot: take CTAs back from the
+    // chain with the least work per CTA
+    while (used > total) {
+        int best = -1;
+        for (int g = 0; g < m; ++g)
+            if (G[g] > 1 && (best < 0 || work(g) < work(best))) best = g;
+        if (best < 0) break;
+        --G[best];
+        --used;
+    }
     while (used < total) {
         int best = -1;
-        double best_w = 0.0;
-        for (int g = 0; g < m; ++g) {
-            if (G[g] >= cap[g]) continue;
-            const double w = (double)cs[g]->N * cs[g]->N / G[g];
-            if (w > best_w) { best_w = w; best = g; }
-        }
+        for (int g = 0; g < m; ++g)
+            if (G[g] < cap[g] && (best < 0 || work(g) > work(best))) best = g;
         if (best < 0) break;
         ++G[best];
         ++used;
     }
+}
+
+extern "C" spl_status_t spl_chains_plan(const int32_t *n_bins, int32_t n, int32_t sms, int32_t blocks_per_sm,
+                                        int32_t *groups) {
+    if (!n_bins || !groups || n < 1 || n > kChainMultiMax || sms < 1 || blocks_per_sm < 1 ||
+        (long long)n > (long long)sms * blocks_per_sm)
+        return SPL_EINVAL;
+    std::vector<int32_t> cap((size_t)n);
+    for (int32_t g = 0; g < n; ++g) {
+        spl_run_plan_t pl;
+        const spl_status_t st = spl_chain_run_plan(n_bins[g], sms, blocks_per_sm, &pl);
+        if (st != SPL_OK) return st;
+        cap[g] = pl.grid;
+    }
+    multi_groups(n_bins, cap.data(), n, sms * blocks_per_sm, groups);
+    return SPL_OK;
 }
 
 extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_t n, double tol, int32_t max_iter,
@@ -1236,8 +1258,14 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
         const int m = std::min<int32_t>(per_launch, n - k0);
         std::memset(&M, 0, sizeof(M));
         M.n = m;
-        int G[kChainMultiMax];
-        multi_groups(chains + k0, m, total, G);
+        int32_t G[kChainMultiMax], Ns[kChainMultiMax], cap[kChainMultiMax];
+        for (int g = 0; g < m; ++g) {
+            const spl_chain *c = chains[k0 + g];
+            Ns[g] = c->N;
+            cap[g] = (int32_t)std::min<long long>(std::min<long long>((long long)c->run_T * c->run_RB, c->run_grid),
+                                                  chain_run_max_grid());
+        }
+        multi_groups(Ns, cap, m, total, G);
         int chunk = 0;
         M.begin[0] = 0;
         for (int g = 0; g < m; ++g) {

@@ -58,7 +58,7 @@ EXPORTED = ["spl_build", "spl_stationary", "spl_batch_stationary", "spl_batch_st
             "spl_mlp_free", "spl_batch_stationary_learned",
             "spl_batch_stationary_learned_host", "spl_gemm_bf16", "spl_chain_time_pass", "spl_chain_time_step", "spl_selftest_bounded_waits", "spl_chain_run_plan",
             "spl_chain_time_build", "spl_batch_spectral", "spl_mc_histograms", "spl_mlp_time_forward", "spl_batch_tune_lookup",
-            "spl_fp32_fma_peak", "spl_chains_stationary"]
+            "spl_fp32_fma_peak", "spl_chains_stationary", "spl_chains_plan"]
 
 _lib = None
 _lock = threading.Lock()
@@ -168,6 +168,8 @@ def lib():
         L.spl_gemm_bf16.restype = ctypes.c_int
         L.spl_chains_stationary.argtypes = [vp, i32, f64, i32, vp, ctypes.POINTER(spl_report_t)]
         L.spl_chains_stationary.restype = ctypes.c_int
+        L.spl_chains_plan.argtypes = [vp, i32, i32, i32, vp]
+        L.spl_chains_plan.restype = ctypes.c_int
         L.spl_fp32_fma_peak.argtypes = [i32, i32, vp, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(i32)]
         L.spl_fp32_fma_peak.restype = ctypes.c_int
         _lib = L
@@ -425,6 +427,16 @@ def chain_run_plan(n_bins: int, sms: int, blocks_per_sm: int) -> dict:
     _check(lib().spl_chain_run_plan(int(n_bins), int(sms), int(blocks_per_sm), ctypes.byref(pl)),
            "spl_chain_run_plan")
     return {k: int(getattr(pl, k)) for k, _ in spl_run_plan_t._fields_}
+
+
+def chains_plan(n_bins, sms: int, blocks_per_sm: int) -> np.ndarray:
+    """spl_chains_plan (host arithmetic, no GPU needed): CTAs per chain of one
+    multi-chain launch."""
+    nb = np.ascontiguousarray(n_bins, dtype=np.int32)
+    out = np.zeros(len(nb), dtype=np.int32)
+    _check(lib().spl_chains_plan(nb.ctypes.data_as(ctypes.c_void_p), len(nb), int(sms), int(blocks_per_sm),
+                                 out.ctypes.data_as(ctypes.c_void_p)), "spl_chains_plan")
+    return out
 
 
 def selftest_bounded_waits(stream=None) -> int:

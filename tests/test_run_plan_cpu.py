@@ -68,3 +68,39 @@ def test_plan_rejects_bad_arguments():
     for args in ((1, 152, 2), (2000, 0, 2), (2000, 152, 0), ((1 << 24) + 1, 152, 2)):
         with pytest.raises(spl.SplError):
             spl.chain_run_plan(*args)
+
+
+# ---------------------------------------------------------------- multi-chain groups
+
+@pytest.mark.parametrize("n_bins,sms,bps", [
+    ([10000] * 12, 152, 2),                                   # the dead-time sweep: 25-26 CTAs each
+    ([18000, 2, 37, 333, 2000, 1024], 152, 2),                # one large chain and tiny ones (floor of 1 each)
+    (list(range(2, 700, 22)), 152, 2),                        # 32 small chains
+    ([5] * 32, 16, 2),                                        # 32 tiny chains on 32 resident CTAs: one each
+    ([16000, 500], 4, 1),
+])
+def test_chains_plan_invariants(n_bins, sms, bps):
+    G = spl.chains_plan(n_bins, sms, bps)
+    total = sms * bps
+    assert G.sum() <= total
+    for g, n in enumerate(n_bins):
+        cap = spl.chain_run_plan(n, sms, bps)["grid"]
+        assert 1 <= G[g] <= cap
+    # the whole GPU is used unless every chain is at its cap
+    caps = np.array([spl.chain_run_plan(n, sms, bps)["grid"] for n in n_bins])
+    assert G.sum() == min(total, caps.sum())
+    # equal sizes get equal shares to within one CTA
+    if len(set(n_bins)) == 1:
+        assert G.max() - G.min() <= 1
+    # more work never gets fewer CTAs (up to the rounding of one CTA)
+    order = np.argsort(n_bins)
+    assert np.all(np.diff(G[order]) >= -1)
+
+
+def test_chains_plan_rejects_bad_arguments():
+    with pytest.raises(spl.SplError):
+        spl.chains_plan([100] * 33, 152, 2)       # more than one launch takes
+    with pytest.raises(spl.SplError):
+        spl.chains_plan([100] * 5, 2, 2)          # more chains than resident CTAs
+    with pytest.raises(spl.SplError):
+        spl.chains_plan([1, 100], 152, 2)         # a chain needs 2 bins
