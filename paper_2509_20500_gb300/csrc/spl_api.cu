@@ -270,7 +270,7 @@ static spl_status_t plan_run(spl_chain *c) {
     SPL_CU(dalloc(&c->run_vb, 2 * (size_t)c->vlen));
     SPL_CU(cudaMemset(c->run_vb, 0, 2 * sizeof(float) * c->vlen));
     SPL_CU(dalloc(&c->run_pi, (size_t)c->N));
-    SPL_CU(dalloc(&c->run_tsum, 2 * (size_t)T));
+    SPL_CU(dalloc(&c->run_tsum, 8 * (size_t)T));   // [2][T][4] warp partials of the tile sums
     c->run_part_cap = (size_t)G * pl.segs * chain_run_tile_cols();
     SPL_CU(dalloc(&c->run_part, c->run_part_cap));
     SPL_CU(dalloc(&c->run_blk, 2 * (size_t)G * 4));

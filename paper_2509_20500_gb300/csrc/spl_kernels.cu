@@ -1315,6 +1315,21 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err
     return *s_flag != 0;
 }
 
+// 16-byte asynchronous global -> shared copies (generic proxy), completed
+// per thread by cp_async_wait<n> (all but the newest n groups).
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 // First unit of CTA b, and the CTA that owns unit u.
 __device__ __forceinline__ long long run_unit0(int b, long long U, int G) { return (long long)b * U / G; }
 __device__ __forceinline__ int run_owner(long long u, long long U, int G) {
@@ -1324,42 +1339,47 @@ __device__ __forceinline__ int run_owner(long long u, long long U, int G) {
 // End of a tile segment of one CTA: the warp partials added in warp order.
 // A tile the CTA covers whole is finished here (y, v and the tile sum, as in
 // run_tile_reduce); a shared tile leaves the CTA's partial in its slot.
+// The pass ran on the unnormalised broadcast vector of the previous step; inv
+// (1 / sum of its y) normalises the column sums here.  The tile sum is left
+// as four warp partials, tdst[4 t + w].
 __device__ __forceinline__ void run_flush(const ChainRunArgs &a, int t, int t_first, int b, bool own_first,
                                           bool own_last, int t_last, const float (&acc)[kRunC],
-                                          float (*wred)[kRunTW], float *red, float *ydst, float *vdst,
+                                          float (*wred)[kRunTW], float inv, float *ydst, float *vdst,
                                           float *tdst) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, N = a.N;
 #pragma unroll
     for (int c = 0; c < kRunC; ++c) wred[wid][32 * c + lane] = acc[c];
     __syncthreads();
     const bool owned = (t != t_first || own_first) && (t != t_last || own_last);
-    float p = 0.f;
     if (tid < kRunTW) {
+        float p = 0.f;
 #pragma unroll
         for (int w = 0; w < kRunW; ++w) p += wred[w][tid];
-    }
-    if (!owned) {
-        if (tid < kRunTW) a.part[((size_t)b * a.segs + (t - t_first)) * kRunTW + tid] = p;
-    } else {
-        const int col = t * kRunTW + tid;
-        if (tid >= kRunTW || col >= N) p = 0.f;
-        if (tid < kRunTW && col < N) {
-            ydst[col] = p;
-            int r = col + a.l;
-            r -= (r >= N) ? N : 0;
-            vdst[r] = p * __ldg(a.rho + r);
+        p *= inv;
+        if (!owned) {
+            a.part[((size_t)b * a.segs + (t - t_first)) * kRunTW + tid] = p;
+        } else {
+            const int col = t * kRunTW + tid;
+            if (col < N) {
+                ydst[col] = p;
+                int r = col + a.l;
+                r -= (r >= N) ? N : 0;
+                vdst[r] = p * __ldg(a.rho + r);
+            } else {
+                p = 0.f;
+            }
+            const float ts = warp_sum(p);
+            if (lane == 0) tdst[4 * t + wid] = ts;
         }
-        const float tsb = block_sum<kRunNT>(p, red);
-        if (tid == 0) tdst[t] = tsb;
     }
-    __syncthreads();   // wred and red are reused
+    __syncthreads();   // wred is reused
 }
 
 // Adds the tile's partials in CTA order (CTA bf may have started in an
 // earlier tile; every later CTA of the tile starts inside it, slot 0) into
 // y_j, writes v_{(j+l) mod N} = y_j rho_{(j+l) mod N} and the tile sum.
 __device__ __forceinline__ void run_tile_reduce(const ChainRunArgs &a, int t, long long U, int G, float *ydst,
-                                                float *vdst, float *tdst, float *red) {
+                                                float *vdst, float *tdst) {
     const int tid = threadIdx.x, N = a.N, RB = a.RB;
     const int bf = run_owner((long long)t * RB, U, G), bl = run_owner((long long)(t + 1) * RB - 1, U, G);
     const int col = t * kRunTW + tid;
@@ -1375,8 +1395,10 @@ __device__ __forceinline__ void run_tile_reduce(const ChainRunArgs &a, int t, lo
         ydst[col] = yv;
         vdst[r] = yv * rr;
     }
-    const float tsb = block_sum<kRunNT>(yv, red);
-    if (tid == 0) tdst[t] = tsb;
+    if (tid < kRunTW) {
+        const float ts = warp_sum(yv);
+        if ((tid & 31) == 0) tdst[4 * t + (tid >> 5)] = ts;
+    }
 }
 
 // Every power step of one chain on the G CTAs of its group; b is this CTA's
@@ -1407,14 +1429,33 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
     const int j0 = min(N, b * S), j1 = min(N, j0 + S);
     const float *vsrc = a.v0;               // h^(0) = pi^(0)_{(k-l) mod N} rho_k
     float inv = 1.f;
+    // windows of this CTA's units, staged as 16-byte async copies into buffer
+    // w & 1 (a.chunk rows each); unit u holds rows (u mod RB) 32 ... + 31
+    constexpr int kWinUnits = kRunMaxChunk / 32;
+    const int nwin = (int)((u1 - u0 + kWinUnits - 1) / kWinUnits);
+    auto stage = [&](int w) {
+        const long long wu0 = u0 + (long long)w * kWinUnits, wu1 = min(u1, wu0 + kWinUnits);
+        const int off0 = (int)(wu0 % RB);
+        const int nq = (int)(wu1 - wu0) * 8;
+        float *dst = sv + (w & 1) * a.chunk;
+        for (int q = tid; q < nq; q += kRunNT) {
+            int o = off0 + (q >> 3);
+            o -= (o / RB) * RB;                     // 32-row block inside its tile
+            cp_async16(dst + 4 * q, vsrc + 4 * (o * 8 + (q & 7)));
+        }
+        cp_async_commit();
+    };
+    stage(0);
     // arrivals expected at the shared first and last tiles, less one
     const int cnt_first = run_owner((long long)(t_first + 1) * RB - 1, U, G) - run_owner((long long)t_first * RB, U, G);
     const int cnt_last = run_owner((long long)(t_last + 1) * RB - 1, U, G) - run_owner((long long)t_last * RB, U, G);
     for (int k = 1;; ++k) {
         float *ydst = a.y + (k & 1) * vlen;
         float *vdst = a.vb + (k & 1) * vlen;
-        float *tdst = a.tsum + (size_t)(k & 1) * T;
+        float *tdst = a.tsum + (size_t)(k & 1) * 4 * T;
         // ---- pass k, in windows of at most kRunMaxChunk rows staged in unit order
+        // into two shared buffers: window w + 1 is in flight while w is summed
+        // (window 0 was issued before the previous step's normalisation)
         int cur_t = t_first;
         float mlo[kRunC], mhi[kRunC], acc[kRunC];
         // the first tile's column factors load with the staging
@@ -1426,28 +1467,21 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             mhi[c] = m * eL;
             acc[c] = 0.f;
         }
-        for (long long wu0 = u0; wu0 < u1; wu0 += kRunMaxChunk / 32) {
-            const long long wu1 = min(u1, wu0 + kRunMaxChunk / 32);
-            const int tw0 = (int)(wu0 / RB);
-            const int off0 = (int)(wu0 - (long long)tw0 * RB);
-            const int nq = (int)(wu1 - wu0) * 8;
-            const float4 *v4 = reinterpret_cast<const float4 *>(vsrc);
-            float4 *s4 = reinterpret_cast<float4 *>(sv);
-            for (int q = tid; q < nq; q += kRunNT) {
-                int o = off0 + (q >> 3);
-                o -= (o / RB) * RB;                     // 32-row block inside its tile
-                float4 x = __ldcg(v4 + o * 8 + (q & 7));
-                x.x *= inv;
-                x.y *= inv;
-                x.z *= inv;
-                x.w *= inv;
-                s4[q] = x;
+        for (int w = 0; w < nwin; ++w) {
+            if (w + 1 < nwin) {
+                stage(w + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
+            const long long wu0 = u0 + (long long)w * kWinUnits, wu1 = min(u1, wu0 + kWinUnits);
+            const int tw0 = (int)(wu0 / RB);
+            const float *wbuf = sv + (w & 1) * a.chunk;
             for (int t = tw0; (long long)t * RB < wu1; ++t) {
                 const long long su0 = max(wu0, (long long)t * RB), su1 = min(wu1, (long long)(t + 1) * RB);
                 if (t != cur_t) {
-                    run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, red, ydst, vdst, tdst);
+                    run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, inv, ydst, vdst, tdst);
 #pragma unroll
                     for (int c = 0; c < kRunC; ++c) {
                         const int col = t * kRunTW + 32 * c + lane;
@@ -1463,7 +1497,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
                 const int nb = rb1 - rb0;
                 const int wb0 = rb0 + (nb * wid) / kRunW, wb1 = rb0 + (nb * (wid + 1)) / kRunW;
                 if (wb1 > wb0) {
-                    const float *vt = sv + ((long long)t * RB - wu0) * 32;   // row r of tile t at vt[r]
+                    const float *vt = wbuf + ((long long)t * RB - wu0) * 32;   // row r of tile t at vt[r]
                     float out[kRunC];
                     tri_pass<kRunC, false, kChain, true, false>(vt, 32 * wb0, 32 * wb1, t * kRunTW, lane, mlo, mhi,
                                                                out);
@@ -1471,9 +1505,9 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
                     for (int c = 0; c < kRunC; ++c) acc[c] += out[c];
                 }
             }
-            __syncthreads();   // sv is restaged
+            __syncthreads();   // this buffer is restaged two windows later
         }
-        run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, red, ydst, vdst, tdst);
+        run_flush(a, cur_t, t_first, b, own_first, own_last, t_last, acc, wred, inv, ydst, vdst, tdst);
         // shared tiles: the last CTA to finish one adds its partials
         __syncthreads();
         if (tid == 0) {
@@ -1490,11 +1524,8 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
         }
         __syncthreads();
         const int lastmask = s_flag;
-        if (lastmask & 1) run_tile_reduce(a, t_first, U, G, ydst, vdst, tdst, red);
-        if (lastmask & 2) {
-            __syncthreads();   // red is reused
-            run_tile_reduce(a, t_last, U, G, ydst, vdst, tdst, red);
-        }
+        if (lastmask & 1) run_tile_reduce(a, t_first, U, G, ydst, vdst, tdst);
+        if (lastmask & 2) run_tile_reduce(a, t_last, U, G, ydst, vdst, tdst);
         if (!grid_sync(a.bar, gen, a.err_flag, &s_flag, b, G)) {
             if (b == 0) {
                 stp->st = st;
@@ -1503,6 +1534,10 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             }
             return;
         }
+        // every h of step k is written: the next pass's first window is staged
+        // while this step is normalised
+        vsrc = vdst;
+        stage(0);
         // ---- normalise step k, and decide on step k-1
         float *pcur = (k & 1) ? a.pi_alt : a.pi;
         const float *pprev = (k & 1) ? a.pi : a.pi_alt;
@@ -1519,7 +1554,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             red5[2] = x0.z + x1.z;
             red5[3] = x0.w + x1.w;
         }
-        for (int t = tid; t < T; t += kRunNT) red5[4] += __ldcg(tdst + t);
+        for (int t = tid; t < 4 * T; t += kRunNT) red5[4] += __ldcg(tdst + t);
         const int jf = j0 + tid;
         float fy = 0.f, fp = 0.f, f1 = 0.f, f2 = 0.f;
         if (jf < j1) {
@@ -1567,12 +1602,12 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
             if ((k - 1) & 1)
                 for (int j = j0 + tid; j < j1; j += kRunNT) a.pi[j] = a.pi_alt[j];
+            cp_async_wait<0>();   // the staged window is not used
             return;
         }
         if (tid == 0)
             reinterpret_cast<float4 *>(a.blk + (size_t)(k & 1) * G * 4)[b] =
                 make_float4(stats[0], stats[1], stats[2], stats[3]);
-        vsrc = vdst;
     }
 }
 
@@ -2066,7 +2101,7 @@ int chain_run_tile_cols() { return kRunTW; }
 int chain_run_bar_words() { return 2 * kBarGen; }
 int chain_run_max_grid() { return 2 * kRunNT; }
 int chain_run_max_chunk() { return kRunMaxChunk; }
-size_t chain_run_smem_bytes(int chunk) { return (size_t)chunk * sizeof(float); }
+size_t chain_run_smem_bytes(int chunk) { return 2 * (size_t)chunk * sizeof(float); }   // two staging buffers
 
 int chain_run_blocks_per_sm(int chunk) {
     const size_t smem = chain_run_smem_bytes(chunk);
