@@ -614,8 +614,8 @@ def run_gpu(args):
                  "iters": mreps["iters"].tolist(),
                  "roofline": {"bound": "alu", "achieved": mt, "peak": peak, "unit": "TFLOP/s", "frac": mt / peak,
                               "work": "2 FLOP x N^2 per power step that the stop rule counts (iters), summed"},
-                 "step_balance": float(mreps["iters"].mean() / mreps["iters"].max()),
-                 "what": "spl_chains_stationary: 12 fused chains, one cooperative launch, ~25 CTAs per chain"}
+                 "what": "spl_chains_stationary: 12 fused chains in lockstep in one cooperative launch "
+                         "(each step's work of the chains still iterating split over all CTAs)"}
         if hrefs is not None:
             mo_h = mo.cpu().numpy().astype(np.float64)
             dd = [np.abs(mo_h[moff[k]:moff[k + 1]] - hrefs[k]) for k in range(len(hx))]

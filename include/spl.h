@@ -347,16 +347,21 @@ SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_p
  * start, for many pixels at once).
  *   chains: n distinct chains built with SPL_FUSED on one and the same stream
  *   (the call runs on that stream).  One cooperative launch (at most 32
- *   chains per launch; more run as consecutive launches) splits the resident
- *   CTAs into one group per chain, sized in proportion to N^2; each group
- *   runs every power step of its chain with its own barrier and stop rule, so
- *   one chain's dependent round trips overlap the others' FMA work.
+ *   chains per launch; more run as consecutive launches) runs the chains in
+ *   lockstep: at every power step the work of the chains still iterating
+ *   (128-column tile x 32-row units, chain after chain) is split evenly over
+ *   all resident CTAs, then their bins likewise for the normalisation, with
+ *   one grid barrier per step.  Each chain has its own stop rule; a chain that
+ *   stops leaves the step's work to the others, so no CTA idles while any
+ *   chain iterates.
  *   d_out: device [sum of n_bins] FP32, the pmfs packed in chain order.
  *   h_reports: NULL or host [n]; with it the call synchronises the stream and
  *   returns the worst per-chain status, without it the call is asynchronous.
  *   Each chain's pmf is the one spl_stationary gives (same steps, same stop
- *   rule; the column pass is partitioned over fewer CTAs, so sums are added
- *   in another order).
+ *   rule; its column pass is split over other CTAs, so sums are added in
+ *   another order).  A chain may need more partial and statistics slots than
+ *   its own single-chain plan: the first such call grows them (a device
+ *   allocation, after a stream synchronisation).
  * Errors: SPL_EINVAL (NULL chain, a materialised chain, a chain given twice,
  * chains on different streams, n < 0, tol <= 0, max_iter < 1), SPL_ENOMEM,
  * SPL_ECUDA; per chain SPL_ENOCONV, SPL_ETIMEOUT as spl_stationary.
@@ -364,15 +369,16 @@ SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_p
 SPL_API spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_t n, double tol, int32_t max_iter,
                                            float *d_out, spl_report_t *h_reports);
 
-/* Group sizes of one multi-chain launch (host arithmetic only, no GPU
- * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident,
- * groups[g] gets the CTAs of chain g (n_bins[g] bins): shares of
- * sms x blocks_per_sm in proportion to n_bins^2, at least 1, at most the
- * chain's own grid (spl_chain_run_plan), the remainder to the chain with the
- * most work per CTA.  1 <= n <= 32 and n <= sms x blocks_per_sm, else
+/* Partial slots per column tile of each chain of a lockstep multi-chain
+ * launch (host arithmetic only, no GPU needed): on a GPU with `sms` SMs
+ * keeping `blocks_per_sm` CTAs resident (grid G = sms x blocks_per_sm), a
+ * step's units are split as [b U / G', (b+1) U / G') over G' = min(G, U) CTAs
+ * with U >= the chain's own units T x RB, so one tile of RB units meets at
+ * most ceil(RB / max(1, floor(T RB / G))) + 1 CTAs (at most RB, at most G);
+ * slots[g] is that bound for chain g (n_bins[g] bins).  1 <= n <= 32, else
  * SPL_EINVAL. */
 SPL_API spl_status_t spl_chains_plan(const int32_t *n_bins, int32_t n, int32_t sms, int32_t blocks_per_sm,
-                                     int32_t *groups);
+                                     int32_t *slots);
 
 /* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
  * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a

@@ -157,6 +157,7 @@ struct spl_chain {
     int *run_ticket = nullptr;
     unsigned *run_bar = nullptr;
     size_t run_part_cap = 0;         // floats of run_part
+    size_t run_blk_cap = 0;          // floats of run_blk
     // kGraphSteps power steps captured once as a CUDA graph, replayed per chunk
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t steps_exec = nullptr;
@@ -273,7 +274,8 @@ static spl_status_t plan_run(spl_chain *c) {
     SPL_CU(dalloc(&c->run_tsum, 8 * (size_t)T));   // [2][T][4] warp partials of the tile sums
     c->run_part_cap = (size_t)G * pl.segs * chain_run_tile_cols();
     SPL_CU(dalloc(&c->run_part, c->run_part_cap));
-    SPL_CU(dalloc(&c->run_blk, 2 * (size_t)G * 4));
+    c->run_blk_cap = 2 * (size_t)G * 4;
+    SPL_CU(dalloc(&c->run_blk, c->run_blk_cap));
     SPL_CU(dalloc(&c->run_ticket, (size_t)T));
     SPL_CU(dalloc(&c->run_bar, (size_t)chain_run_bar_words()));
     SPL_CU(cudaMemset(c->run_ticket, 0, sizeof(int) * T));
@@ -1179,55 +1181,13 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
     return SPL_OK;
 }
 
-// Group sizes of a multi-chain launch: `total` resident CTAs shared in
-// proportion to each chain's work per pass (N^2), at least one each, at most
-// cap[g] each (the chain's own grid: at most one CTA per work unit); the CTAs
-// left over go one at a time to the chain with the most work per CTA.  With
-// m <= total every chain keeps at least one CTA and the sum never exceeds
-// total.
-static void multi_groups(const int32_t *N, const int32_t *cap, int m, int total, int32_t *G) {
-    double W = 0.0;
-    for (int g = 0; g < m; ++g) W += (double)N[g] * N[g];
-    auto work = [&](int g) { return (double)N[g] * N[g] / G[g]; };
-    int used = 0;
-    for (int g = 0; g < m; ++g) {
-        const double share = (double)total * N[g] * (double)N[g] / W;
-        G[g] = std::max(1, std::min(cap[g], (int)share));
-        used += G[g];
-    }
-    // the floor of one CTA per chain may overshoot: take CTAs back from the
-    // chain with the least work per CTA
-    while (used > total) {
-        int best = -1;
-        for (int g = 0; g < m; ++g)
-            if (G[g] > 1 && (best < 0 || work(g) < work(best))) best = g;
-        if (best < 0) break;
-        --G[best];
-        --used;
-    }
-    while (used < total) {
-        int best = -1;
-        for (int g = 0; g < m; ++g)
-            if (G[g] < cap[g] && (best < 0 || work(g) > work(best))) best = g;
-        if (best < 0) break;
-        ++G[best];
-        ++used;
-    }
-}
-
 extern "C" spl_status_t spl_chains_plan(const int32_t *n_bins, int32_t n, int32_t sms, int32_t blocks_per_sm,
-                                        int32_t *groups) {
-    if (!n_bins || !groups || n < 1 || n > kChainMultiMax || sms < 1 || blocks_per_sm < 1 ||
-        (long long)n > (long long)sms * blocks_per_sm)
-        return SPL_EINVAL;
-    std::vector<int32_t> cap((size_t)n);
+                                        int32_t *slots) {
+    if (!n_bins || !slots || n < 1 || n > kChainMultiMax || sms < 1 || blocks_per_sm < 1) return SPL_EINVAL;
     for (int32_t g = 0; g < n; ++g) {
-        spl_run_plan_t pl;
-        const spl_status_t st = spl_chain_run_plan(n_bins[g], sms, blocks_per_sm, &pl);
-        if (st != SPL_OK) return st;
-        cap[g] = pl.grid;
+        if (n_bins[g] < 2 || n_bins[g] > kMaxBins) return SPL_EINVAL;
+        slots[g] = chain_multi_slots(n_bins[g], sms * blocks_per_sm);
     }
-    multi_groups(n_bins, cap.data(), n, sms * blocks_per_sm, groups);
     return SPL_OK;
 }
 
@@ -1239,7 +1199,7 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
         if (!chains[k] || chains[k]->mode != SPL_FUSED || chains[k]->stream != chains[0]->stream) return SPL_EINVAL;
     for (int32_t k = 0; k < n; ++k)
         for (int32_t j = 0; j < k; ++j)
-            if (chains[j] == chains[k]) return SPL_EINVAL;   // one chain's buffers cannot serve two groups
+            if (chains[j] == chains[k]) return SPL_EINVAL;   // one chain's buffers hold one iteration
     BatchWorkspace *ws = nullptr;
     spl_status_t st = ws_get(&ws);
     if (st != SPL_OK) return st;
@@ -1249,51 +1209,54 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
     if (e != cudaSuccess) return status_of_alloc(e, "reports");
     const int bps = std::min(2, chain_multi_blocks_per_sm(chain_run_max_chunk()));
     if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "multi-chain occupancy");
-    const int total = bps * num_sms_current();
-    const int per_launch = std::min(kChainMultiMax, total);
+    const int grid = bps * num_sms_current();
     static_assert(sizeof(ChainMultiArgs) < 30000, "kernel parameter size");
     ChainMultiArgs M;
     int64_t off = 0;
-    for (int32_t k0 = 0; k0 < n; k0 += per_launch) {
-        const int m = std::min<int32_t>(per_launch, n - k0);
+    for (int32_t k0 = 0; k0 < n; k0 += kChainMultiMax) {
+        const int m = std::min<int32_t>(kChainMultiMax, n - k0);
         std::memset(&M, 0, sizeof(M));
         M.n = m;
-        int32_t G[kChainMultiMax], Ns[kChainMultiMax], cap[kChainMultiMax];
-        for (int g = 0; g < m; ++g) {
-            const spl_chain *c = chains[k0 + g];
-            Ns[g] = c->N;
-            cap[g] = (int32_t)std::min<long long>(std::min<long long>((long long)c->run_T * c->run_RB, c->run_grid),
-                                                  chain_run_max_grid());
-        }
-        multi_groups(Ns, cap, m, total, G);
-        int chunk = 0;
-        M.begin[0] = 0;
+        M.bar = chains[k0]->run_bar;
+        M.tol_err = (float)(0.5 * tol);
+        M.min_iter = 1;
+        M.max_iter = max_iter;
+        long long U = 0;
         for (int g = 0; g < m; ++g) {
             spl_chain *c = chains[k0 + g];
-            const long long U = (long long)c->run_T * c->run_RB;
-            int segs = 1;
-            long long umax = 0;
-            run_partition(U, c->run_RB, G[g], &segs, &umax);
-            const size_t need = (size_t)G[g] * segs * chain_run_tile_cols();
-            if (need > c->run_part_cap) {
-                // a smaller group covers more tiles per CTA: more partial slots
-                float *np = nullptr;
-                if ((e = dalloc(&np, need)) != cudaSuccess) return status_of_alloc(e, "chain partials");
-                SPL_CU(cudaStreamSynchronize(c->stream));
-                cudaFree(c->run_part);
-                c->run_part = np;
-                c->run_part_cap = need;
+            U += (long long)c->run_T * c->run_RB;
+            const int slots = chain_multi_slots(c->N, grid);
+            const size_t need_part = (size_t)c->run_T * slots * chain_run_tile_cols();
+            const size_t need_blk = 2 * (size_t)grid * 4;
+            if (need_part > c->run_part_cap || need_blk > c->run_blk_cap) {
+                // more partial slots or statistics slots than the chain's own plan
+                SPL_CU(cudaStreamSynchronize(s));
+                if (need_part > c->run_part_cap) {
+                    float *np = nullptr;
+                    if ((e = dalloc(&np, need_part)) != cudaSuccess) return status_of_alloc(e, "chain partials");
+                    cudaFree(c->run_part);
+                    c->run_part = np;
+                    c->run_part_cap = need_part;
+                }
+                if (need_blk > c->run_blk_cap) {
+                    float *nb = nullptr;
+                    if ((e = dalloc(&nb, need_blk)) != cudaSuccess) return status_of_alloc(e, "chain statistics");
+                    cudaFree(c->run_blk);
+                    c->run_blk = nb;
+                    c->run_blk_cap = need_blk;
+                }
             }
             ChainRunArgs a = run_args(c);
-            a.segs = segs;
-            a.chunk = (int)std::min<long long>(chain_run_max_chunk(), umax * 32);
-            chunk = std::max(chunk, a.chunk);
+            a.segs = slots;
             M.c[g] = a;
             M.off[g] = off;
             off += c->N;
-            M.begin[g + 1] = M.begin[g] + G[g];
         }
-        SPL_CU(launch_chain_multi(M, M.begin[m], chunk, (float)(0.5 * tol), max_iter, d_out, ws->reps + k0, s));
+        // rows of one staging buffer: a window is at most chain_run_max_chunk()
+        // rows and at most one CTA's share of the first step's units
+        const long long per_cta = (U + std::min<long long>(grid, U) - 1) / std::min<long long>(grid, U);
+        M.chunk = (int)std::min<long long>(chain_run_max_chunk(), 32 * per_cta);
+        SPL_CU(launch_chain_multi(M, grid, d_out, ws->reps + k0, s));
     }
     if (!h_reports) return SPL_OK;
     e = grow_host(&ws->h_reps, &ws->h_reps_cap, (size_t)n);

@@ -1615,22 +1615,410 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
     chain_run_body(a, blockIdx.x, gridDim.x);
 }
 
-// Several chains in one cooperative launch: chain g runs on CTAs
-// [begin[g], begin[g+1]) with its own barrier, tickets and stop rule, so one
-// chain's dependent L2 round trips (staging, tickets, barrier, normalisation)
-// overlap the other chains' FMA loops.  The groups never wait on one another.
+// Several chains in lockstep in one cooperative launch.  Step k of every
+// chain still iterating runs in the same pass: the units of the active chains
+// (the chain's 128-column tiles x 32-row blocks, chain after chain) are split
+// evenly over the CTAs, each CTA leaves one partial per tile it touches and
+// the last CTA to finish a shared tile adds them in CTA order; after one grid
+// barrier the active chains' bins, chain after chain, are split evenly over
+// the CTAs for the normalisation.  Every CTA keeps an identical copy of each
+// chain's stop state and takes the same decisions (on step k - 1, one pass
+// after it, as the single-chain kernel), so all CTAs drop a chain at the same
+// step and re-split the work of the others.
+
+__device__ __forceinline__ long long lk_owner(long long u, long long U, int G) {
+    return ((u + 1) * G + U - 1) / U - 1;
+}
+
+// Flush of tile t of chain g at the end of this CTA's segment of it: the warp
+// partials added in warp order and normalised by inv; a tile that only this
+// CTA touches is finished (y, v, the tile sum as four warp partials), a shared
+// tile leaves this CTA's partial in slot b - bf.
+__device__ __forceinline__ void lk_flush(const ChainRunArgs &c, int t, int k, bool owned, int slot,
+                                         const float (&acc)[kRunC], float (*wred)[kRunTW], float inv) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, N = c.N;
+#pragma unroll
+    for (int q = 0; q < kRunC; ++q) wred[wid][32 * q + lane] = acc[q];
+    __syncthreads();
+    if (tid < kRunTW) {
+        float p = 0.f;
+#pragma unroll
+        for (int w = 0; w < kRunW; ++w) p += wred[w][tid];
+        p *= inv;
+        if (!owned) {
+            c.part[((size_t)t * c.segs + slot) * kRunTW + tid] = p;
+        } else {
+            const int col = t * kRunTW + tid;
+            if (col < N) {
+                c.y[(size_t)(k & 1) * c.vlen + col] = p;
+                int r = col + c.l;
+                r -= (r >= N) ? N : 0;
+                c.vb[(size_t)(k & 1) * c.vlen + r] = p * __ldg(c.rho + r);
+            } else {
+                p = 0.f;
+            }
+            const float ts = warp_sum(p);
+            if (lane == 0) c.tsum[(size_t)(k & 1) * 4 * c.T + 4 * t + wid] = ts;
+        }
+    }
+    __syncthreads();   // wred is reused
+}
+
+// The last CTA to finish shared tile t adds slots 0 .. nslot-1 in CTA order.
+__device__ __forceinline__ void lk_tile_reduce(const ChainRunArgs &c, int t, int k, int nslot) {
+    const int tid = threadIdx.x, N = c.N;
+    const int col = t * kRunTW + tid;
+    float yv = 0.f;
+    if (tid < kRunTW && col < N) {
+        int r = col + c.l;
+        r -= (r >= N) ? N : 0;
+        const float *pp = c.part + (size_t)t * c.segs * kRunTW + tid;
+        yv = __ldcg(pp);
+#pragma unroll 4
+        for (int q = 1; q < nslot; ++q) yv += __ldcg(pp + (size_t)q * kRunTW);
+        c.y[(size_t)(k & 1) * c.vlen + col] = yv;
+        c.vb[(size_t)(k & 1) * c.vlen + r] = yv * __ldg(c.rho + r);
+    }
+    if (tid < kRunTW) {
+        const float ts = warp_sum(yv);
+        if ((tid & 31) == 0) c.tsum[(size_t)(k & 1) * 4 * c.T + 4 * t + (tid >> 5)] = ts;
+    }
+}
+
 __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_constant__ ChainMultiArgs m) {
-    int g = 0;
-    while (g + 1 < m.n && (int)blockIdx.x >= m.begin[g + 1]) ++g;
-    chain_run_body(m.c[g], (int)blockIdx.x - m.begin[g], m.begin[g + 1] - m.begin[g]);
+    extern __shared__ float4 smem4[];
+    float *sv = reinterpret_cast<float *>(smem4);
+    __shared__ float wred[kRunW][kRunTW];
+    __shared__ float red[5 * kRunW + 5];
+    __shared__ int s_flag;
+    __shared__ long long s_ub[3][kChainMultiMax + 1];   // unit bases of the chains in step k's pass: slot k % 3
+    __shared__ long long s_nb[3][kChainMultiMax + 1];   // bin bases (the normalisation of step k)
+    __shared__ unsigned s_mask[3];                      // chains in step k's pass
+    __shared__ float s_inv[kChainMultiMax];             // 1 / sum of y of each chain's last step
+    __shared__ float s_eL[kChainMultiMax];
+    __shared__ StopState s_st[kChainMultiMax];
+    __shared__ int s_fin[kChainMultiMax];
+    __shared__ int s_tile[6];                           // shared first / last tile: chain, tile, slots
+    constexpr int kWinUnits = kRunMaxChunk / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int G = gridDim.x, b = blockIdx.x, n = m.n;
+    unsigned gen = 0u;
+
+    // thread 0: unit and bin bases of the chains in `mask`, into slot sl
+    auto bases = [&](int sl, unsigned mask) {
+        long long u = 0, j = 0;
+        for (int g = 0; g < n; ++g) {
+            s_ub[sl][g] = u;
+            s_nb[sl][g] = j;
+            if (mask >> g & 1u) {
+                u += (long long)m.c[g].T * m.c[g].RB;
+                j += m.c[g].N;
+            }
+        }
+        s_ub[sl][n] = u;
+        s_nb[sl][n] = j;
+        s_mask[sl] = mask;
+    };
+    // this CTA's units [u0, u1) of step slot sl (all CTAs below min(G, U) get at least one)
+    auto range = [&](int sl, long long &u0, long long &u1) {
+        const long long U = s_ub[sl][n];
+        const int Ge = (int)min((long long)G, U);
+        u0 = b < Ge ? (long long)b * U / Ge : 0;
+        u1 = b < Ge ? (long long)(b + 1) * U / Ge : 0;
+    };
+    // the chain holding unit u (chains without units this step are skipped)
+    auto chain_of = [&](int sl, long long u) {
+        int q = 0;
+        while (s_ub[sl][q + 1] <= u) ++q;
+        return q;
+    };
+    // windows: at most kWinUnits units of one chain, in unit order
+    auto win_first = [&](int sl, long long u0, long long u1, int &g, long long &lw0, long long &lw1) {
+        if (u0 >= u1) return false;
+        g = chain_of(sl, u0);
+        lw0 = u0 - s_ub[sl][g];
+        lw1 = min(lw0 + kWinUnits, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
+        return true;
+    };
+    auto win_next = [&](int sl, long long u1, int &g, long long &lw0, long long &lw1) {
+        const long long end = min(u1, s_ub[sl][g + 1]) - s_ub[sl][g];
+        if (lw1 < end) {
+            lw0 = lw1;
+            lw1 = min(lw0 + kWinUnits, end);
+            return true;
+        }
+        if (s_ub[sl][g + 1] >= u1) return false;
+        g = chain_of(sl, s_ub[sl][g + 1]);
+        lw0 = 0;
+        lw1 = min((long long)kWinUnits, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
+        return true;
+    };
+    // 16-byte async copies of a window's rows into buffer buf; step k reads
+    // the start vector (k = 1) or the previous step's broadcast vector
+    auto stage = [&](int g, long long lw0, long long lw1, int buf, int k) {
+        const ChainRunArgs &c = m.c[g];
+        const float *src = k == 1 ? c.v0 : c.vb + (size_t)((k - 1) & 1) * c.vlen;
+        const int RB = c.RB;
+        const int off0 = (int)(lw0 % RB);
+        const int nq = (int)(lw1 - lw0) * 8;
+        float *dst = sv + (size_t)buf * m.chunk;
+        for (int q = tid; q < nq; q += kRunNT) {
+            int o = off0 + (q >> 3);
+            o -= (o / RB) * RB;                     // 32-row block inside its tile
+            cp_async16(dst + 4 * q, src + 4 * (o * 8 + (q & 7)));
+        }
+        cp_async_commit();
+    };
+
+    if (tid < n) {
+        s_st[tid] = m.c[tid].state->st;
+        s_inv[tid] = 1.f;
+        s_eL[tid] = (float)m.c[tid].scal[1];
+    }
+    if (tid == 0) bases(1, n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u));
+    __syncthreads();
+    {
+        long long u0, u1, lw0, lw1;
+        int g;
+        range(1, u0, u1);
+        if (win_first(1, u0, u1, g, lw0, lw1)) stage(g, lw0, lw1, 0, 1);
+    }
+
+    for (int k = 1;; ++k) {
+        const int sl = k % 3;
+        const unsigned mask = s_mask[sl];
+        const long long U = s_ub[sl][n];
+        const int Ge = (int)min((long long)G, U);
+        long long u0, u1;
+        range(sl, u0, u1);
+        // ---- pass k over this CTA's units; window 0 is already in flight
+        int cur_g = -1, cur_t = -1;
+        float mlo[kRunC], mhi[kRunC], acc[kRunC];
+        auto flush = [&]() {
+            const ChainRunArgs &c = m.c[cur_g];
+            const long long tu = s_ub[sl][cur_g] + (long long)cur_t * c.RB;
+            const int bf = (int)lk_owner(tu, U, Ge), bl = (int)lk_owner(tu + c.RB - 1, U, Ge);
+            const int slot = b - bf;
+            if (bf != bl && slot >= c.segs) {          // outside the partial slots: report, write nothing
+                if (tid == 0) atomicExch(m.c[0].err_flag, 1);
+                return;
+            }
+            lk_flush(c, cur_t, k, bf == bl, slot, acc, wred, s_inv[cur_g]);
+        };
+        int g;
+        long long lw0, lw1;
+        bool more = win_first(sl, u0, u1, g, lw0, lw1);
+        for (int wi = 0; more; ++wi) {
+            int ng = g;
+            long long nw0 = lw0, nw1 = lw1;
+            const bool has_next = win_next(sl, u1, ng, nw0, nw1);
+            if (has_next) {
+                stage(ng, nw0, nw1, (wi + 1) & 1, k);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const ChainRunArgs &c = m.c[g];
+            const int RB = c.RB, N = c.N;
+            const float *wbuf = sv + (size_t)(wi & 1) * m.chunk;
+            for (int t = (int)(lw0 / RB); (long long)t * RB < lw1; ++t) {
+                const long long su0 = max(lw0, (long long)t * RB), su1 = min(lw1, (long long)(t + 1) * RB);
+                if (t != cur_t || g != cur_g) {
+                    if (cur_g >= 0) flush();
+#pragma unroll
+                    for (int q = 0; q < kRunC; ++q) {
+                        const int col = t * kRunTW + 32 * q + lane;
+                        const float x = col < N ? __ldg(c.w + col) : 0.f;
+                        mlo[q] = x;
+                        mhi[q] = x * s_eL[g];
+                        acc[q] = 0.f;
+                    }
+                    cur_g = g;
+                    cur_t = t;
+                }
+                // warp wid takes 32-row blocks [wb0, wb1) of the segment
+                const int rb0 = (int)(su0 - (long long)t * RB), rb1 = (int)(su1 - (long long)t * RB);
+                const int nb = rb1 - rb0;
+                const int wb0 = rb0 + (nb * wid) / kRunW, wb1 = rb0 + (nb * (wid + 1)) / kRunW;
+                if (wb1 > wb0) {
+                    const float *vt = wbuf + ((long long)t * RB - lw0) * 32;   // row r of tile t at vt[r]
+                    float out[kRunC];
+                    tri_pass<kRunC, false, kChain, true, false>(vt, 32 * wb0, 32 * wb1, t * kRunTW, lane, mlo, mhi,
+                                                               out);
+#pragma unroll
+                    for (int q = 0; q < kRunC; ++q) acc[q] += out[q];
+                }
+            }
+            __syncthreads();   // this buffer is restaged two windows later
+            g = ng;
+            lw0 = nw0;
+            lw1 = nw1;
+            more = has_next;
+        }
+        if (cur_g >= 0) flush();
+        // shared first / last tile of the range: the last CTA to finish one adds its partials
+        __syncthreads();
+        if (tid == 0) {
+            int mask2 = 0;
+            if (u0 < u1) {
+                long long ue[2] = {u0, u1 - 1};
+                int prev_g = -1, prev_t = -1;
+                for (int e = 0; e < 2; ++e) {
+                    const int q = chain_of(sl, ue[e]);
+                    const ChainRunArgs &c = m.c[q];
+                    const int t = (int)((ue[e] - s_ub[sl][q]) / c.RB);
+                    if (q == prev_g && t == prev_t) break;
+                    prev_g = q;
+                    prev_t = t;
+                    const long long tu = s_ub[sl][q] + (long long)t * c.RB;
+                    const int bf = (int)lk_owner(tu, U, Ge), bl = (int)lk_owner(tu + c.RB - 1, U, Ge);
+                    if (bf == bl) continue;
+                    __threadfence();
+                    const int old = atomicAdd(c.tile_ticket + t, 1);
+                    if (old == bl - bf) {
+                        c.tile_ticket[t] = 0;
+                        __threadfence();
+                        mask2 |= 1 << e;
+                        s_tile[3 * e] = q;
+                        s_tile[3 * e + 1] = t;
+                        s_tile[3 * e + 2] = min(bl - bf + 1, c.segs);
+                    }
+                }
+            }
+            s_flag = mask2;
+        }
+        __syncthreads();
+        const int lastmask = s_flag;
+        if (lastmask & 1) lk_tile_reduce(m.c[s_tile[0]], s_tile[1], k, s_tile[2]);
+        if (lastmask & 2) lk_tile_reduce(m.c[s_tile[3]], s_tile[4], k, s_tile[5]);
+        if (!grid_sync(m.bar, gen, m.c[0].err_flag, &s_flag, b, G)) {
+            if (tid < n) {
+                *m.c[tid].err_flag = 1;
+                if (b == 0) {
+                    ChainState *stp = m.c[tid].state;
+                    stp->st = s_st[tid];
+                    stp->done = 1;
+                    stp->status = ST_ENOCONV;
+                }
+            }
+            return;
+        }
+        // ---- step k is complete: per chain (one warp each) the sum of y and,
+        // from the statistics the CTAs left in step k - 1's normalisation, the
+        // decision on step k - 1
+        const int pk = (k + 2) % 3;
+        for (int q = wid; q < n; q += kRunW) {
+            if (!(mask >> q & 1u)) continue;
+            const ChainRunArgs &c = m.c[q];
+            const float *ts = c.tsum + (size_t)(k & 1) * 4 * c.T;
+            float sy = 0.f;
+            for (int i = lane; i < 4 * c.T; i += 32) sy += __ldcg(ts + i);
+            sy = warp_sum(sy);
+            float sx = 0.f, sd = 0.f, s1 = 0.f, s2 = 0.f;
+            if (k >= 2) {
+                const long long NB = s_nb[pk][n], j0 = s_nb[pk][q];
+                const int GeN = (int)min((long long)G, NB);
+                const int bF = (int)lk_owner(j0, NB, GeN), bL = (int)lk_owner(j0 + c.N - 1, NB, GeN);
+                const float4 *bs = reinterpret_cast<const float4 *>(c.blk + (size_t)((k - 1) & 1) * G * 4);
+                for (int i = bF + lane; i <= bL; i += 32) {
+                    const float4 x = __ldcg(bs + i);
+                    sx += x.x;
+                    sd += x.y;
+                    s1 += x.z;
+                    s2 += x.w;
+                }
+                sx = warp_sum(sx);
+                sd = warp_sum(sd);
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+            }
+            if (lane == 0) {
+                s_inv[q] = 1.f / sy;
+                int fin = 0;
+                if (k >= 2) {
+                    const int su = stop_update(s_st[q], sx, sd, s1, s2, m.tol_err, m.min_iter);
+                    if (su != STOP_CONTINUE) fin = su == STOP_CONVERGED ? 1 : 2;
+                    else if (s_st[q].k >= m.max_iter) fin = 2;
+                }
+                s_fin[q] = fin;
+            }
+        }
+        __syncthreads();
+        unsigned next = mask;
+        for (int q = 0; q < n; ++q)
+            if ((mask >> q & 1u) && s_fin[q]) next &= ~(1u << q);
+        if (b == 0 && tid < n && (mask >> tid & 1u) && s_fin[tid]) {
+            ChainState *stp = m.c[tid].state;
+            stp->st = s_st[tid];
+            stp->done = 1;
+            stp->status = s_fin[tid] == 1 ? ST_OK : ST_ENOCONV;
+        }
+        // the next step's partition, and its first window staged while this
+        // step is normalised
+        if (next) {
+            if (tid == 0) bases((k + 1) % 3, next);
+            __syncthreads();
+            long long v0, v1, w0, w1;
+            int q;
+            range((k + 1) % 3, v0, v1);
+            if (win_first((k + 1) % 3, v0, v1, q, w0, w1)) stage(q, w0, w1, 0, k + 1);
+        }
+        // ---- normalise step k over this CTA's bins of the chains in the pass;
+        // a chain decided on step k - 1 instead keeps pi^(k-1) as its result
+        {
+            const long long NB = s_nb[sl][n];
+            const int GeN = (int)min((long long)G, NB);
+            if (b < GeN) {
+                const long long j0 = (long long)b * NB / GeN, j1 = (long long)(b + 1) * NB / GeN;
+                for (int q = 0; q < n; ++q) {
+                    if (!(mask >> q & 1u)) continue;
+                    const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
+                    if (cb1 <= j0 || cb0 >= j1) continue;
+                    const ChainRunArgs &c = m.c[q];
+                    const int a0 = (int)(max(j0, cb0) - cb0), a1 = (int)(min(j1, cb1) - cb0);
+                    if (s_fin[q]) {
+                        // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
+                        if ((k - 1) & 1)
+                            for (int j = a0 + tid; j < a1; j += kRunNT) c.pi[j] = __ldcg(c.pi_alt + j);
+                        continue;
+                    }
+                    float *pcur = (k & 1) ? c.pi_alt : c.pi;
+                    const float *pprev = (k & 1) ? c.pi : c.pi_alt;
+                    const float *yk = c.y + (size_t)(k & 1) * c.vlen;
+                    const float inv = s_inv[q];
+                    float stats[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int j = a0 + tid; j < a1; j += kRunNT) {
+                        const float pn = __ldcg(yk + j) * inv;
+                        // written by whichever CTA held bin j in the last step (L2 loads)
+                        const float d = pn - __ldcg(pprev + j);
+                        const float f1 = __ldcg(c.d1 + j);
+                        stats[0] += fabsf(d);
+                        stats[1] = fmaf(d, d, stats[1]);
+                        stats[2] = fmaf(d, f1, stats[2]);
+                        stats[3] = fmaf(d, __ldcg(c.d2 + j), stats[3]);
+                        c.d2[j] = f1;
+                        c.d1[j] = d;
+                        pcur[j] = pn;
+                    }
+                    block_sum_k<kRunNT, 4>(stats, red);
+                    if (tid == 0)
+                        reinterpret_cast<float4 *>(c.blk + (size_t)(k & 1) * G * 4)[b] =
+                            make_float4(stats[0], stats[1], stats[2], stats[3]);
+                }
+            }
+        }
+        if (!next) return;   // every chain decided (no window was staged)
+        __syncthreads();
+    }
 }
 
 // Start of a multi-chain iteration, one block per chain: uniform pi^(0) (as
 // init_iter_kernel without a warm start), cleared step vectors, the first
 // broadcast vector h_k = pi^(0)_{(k-l) mod N} rho_k, the stop state, and the
-// chain's error flag, tile tickets and barrier words zeroed.
-__global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_constant__ ChainMultiArgs m,
-                                                                  float tol_err, int max_iter) {
+// chain's error flag and tile tickets zeroed (block 0 also the launch's
+// barrier words).
+__global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_constant__ ChainMultiArgs m) {
     const ChainRunArgs &a = m.c[blockIdx.x];
     const int N = a.N, tid = threadIdx.x;
     const float p0 = 1.f / (float)N;
@@ -1644,7 +2032,8 @@ __global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_c
         v0[k] = k < N ? p0 * a.rho[k] : 0.f;
     }
     for (int t = tid; t < a.T; t += kRunNT) a.tile_ticket[t] = 0;
-    for (int q = tid; q < 2 * kBarGen; q += kRunNT) a.bar[q] = 0u;
+    if (blockIdx.x == 0)
+        for (int q = tid; q < 2 * kBarGen; q += kRunNT) m.bar[q] = 0u;
     if (tid == 0) {
         *a.err_flag = 0;
         ChainState *stp = a.state;
@@ -1653,9 +2042,9 @@ __global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_c
         stp->st = st;
         stp->done = 0;
         stp->status = ST_ENOCONV;
-        stp->tol_err = tol_err;
-        stp->max_iter = max_iter;
-        stp->min_iter = 1;
+        stp->tol_err = m.tol_err;
+        stp->max_iter = m.max_iter;
+        stp->min_iter = m.min_iter;
     }
 }
 
@@ -2123,12 +2512,11 @@ cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s) {
                                        params, smem, s);
 }
 
-cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, int chunk, float tol_err, int max_iter,
-                               float *out, ReportDev *reps, cudaStream_t s) {
-    chain_multi_init_kernel<<<m.n, kRunNT, 0, s>>>(m, tol_err, max_iter);
+cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, float *out, ReportDev *reps, cudaStream_t s) {
+    chain_multi_init_kernel<<<m.n, kRunNT, 0, s>>>(m);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = chain_run_smem_bytes(chunk);
+    const size_t smem = chain_run_smem_bytes(m.chunk);
     e = cudaFuncSetAttribute(chain_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *params[] = {const_cast<ChainMultiArgs *>(&m)};
@@ -2137,6 +2525,14 @@ cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, int chunk, flo
     if (e != cudaSuccess) return e;
     chain_multi_finish_kernel<<<m.n, kRunNT, 0, s>>>(m, out, reps);
     return cudaGetLastError();
+}
+
+int chain_multi_slots(int n_bins, int grid) {
+    const long long T = (n_bins + kRunTW - 1) / kRunTW, RB = split_pad_len(n_bins) / 32;
+    // every CTA of a lockstep partition gets at least max(1, floor(T RB / grid)) units
+    const long long umin = T * RB / grid;
+    const long long slots = umin >= 1 ? (RB + umin - 1) / umin + 1 : RB;
+    return (int)(slots < grid ? slots : grid);
 }
 
 int chain_multi_blocks_per_sm(int chunk) {

@@ -101,16 +101,22 @@ struct ChainRunArgs {
     int *err_flag;           // set if a CTA gave up waiting at the barrier
 };
 
-// Several fused chains in one cooperative launch (at most kChainMultiMax):
-// chain g runs on CTAs [begin[g], begin[g+1]) with the partition of its
-// column pass planned for that group size (c[g].segs, c[g].chunk), and its
-// result goes to out + off[g].
+// Several fused chains in one cooperative launch (at most kChainMultiMax),
+// in lockstep: at every power step the work units of the chains still
+// iterating are numbered one chain after the other and split evenly over all
+// CTAs (and their bins likewise for the normalisation), so a chain that
+// stops leaves no CTA idle.  c[g].segs is the number of partial slots per
+// column tile of chain g; c[g].blk holds [2][grid][4] statistics; c[g].bar is
+// unused (the launch has one barrier, bar).  Results go to out + off[g].
 constexpr int kChainMultiMax = 32;
 struct ChainMultiArgs {
     ChainRunArgs c[kChainMultiMax];
     int64_t off[kChainMultiMax];
-    int begin[kChainMultiMax + 1];
     int n;
+    int chunk;               // rows per staging buffer
+    unsigned *bar;           // [chain_run_bar_words()] grid barrier words, zeroed by the start kernel
+    float tol_err;
+    int min_iter, max_iter;
 };
 
 int chain_run_tile_cols();
@@ -125,8 +131,10 @@ cudaError_t launch_chain_run(const ChainRunArgs &a, int grid, cudaStream_t s);
 // max_iter, cleared tickets, barrier and error flag), the cooperative launch
 // of `grid` CTAs with `chunk` rows of shared staging, and the finish kernel
 // (results to out, reports to reps if not NULL).
-cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, int chunk, float tol_err, int max_iter,
-                               float *out, ReportDev *reps, cudaStream_t s);
+cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, float *out, ReportDev *reps, cudaStream_t s);
+// Partial slots per column tile that chain g needs when its units are part
+// of a lockstep partition over `grid` CTAs.
+int chain_multi_slots(int n_bins, int grid);
 int chain_multi_blocks_per_sm(int chunk);
 // Waits that run out on purpose (status[0]: the mbarrier wait gave up;
 // status[1]: CTAs that left the grid barrier on the abort; err_flag set by the

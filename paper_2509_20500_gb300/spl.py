@@ -430,8 +430,8 @@ def chain_run_plan(n_bins: int, sms: int, blocks_per_sm: int) -> dict:
 
 
 def chains_plan(n_bins, sms: int, blocks_per_sm: int) -> np.ndarray:
-    """spl_chains_plan (host arithmetic, no GPU needed): CTAs per chain of one
-    multi-chain launch."""
+    """spl_chains_plan (host arithmetic, no GPU needed): partial slots per
+    column tile of each chain of a lockstep multi-chain launch."""
     nb = np.ascontiguousarray(n_bins, dtype=np.int32)
     out = np.zeros(len(nb), dtype=np.int32)
     _check(lib().spl_chains_plan(nb.ctypes.data_as(ctypes.c_void_p), len(nb), int(sms), int(blocks_per_sm),

@@ -191,10 +191,10 @@ def test_highres_materialized_and_fused(spl, highres_refs, k):
 
 def test_chains_multi_launch_sweep_vs_oracle(spl, highres_refs):
     """The 12 sweep pixels solved together (spl_chains_stationary: one
-    cooperative launch, one CTA group of about 25 CTAs per chain): every pmf
-    within the tolerance of the oracle, the same step counts as the chain
-    solved alone within one step, and a second call gives the same pmfs bit
-    for bit (groups add their partials in a fixed order)."""
+    cooperative launch, every step's work of the chains still iterating split
+    over all CTAs): every pmf within the tolerance of the oracle, the same
+    step counts as the chain solved alone within one step, and a second call
+    gives the same pmfs bit for bit (partials are added in a fixed order)."""
     px, refs = highres_refs
     cs = spl.ChainSet(px)
     out, off, reps = cs.stationary(tol=1e-6, max_iter=500)
@@ -214,10 +214,11 @@ def test_chains_multi_launch_sweep_vs_oracle(spl, highres_refs):
 
 
 def test_chains_multi_launch_mixed_sizes_and_many_chains(spl):
-    """Ragged sizes in one launch (N = 2 ... 18000; the large chain's group
-    stages several shared-memory windows per CTA) and more chains than one
-    launch takes (40 > 32: two consecutive launches), each against the
-    reparameterised oracle with the same shift."""
+    """Ragged sizes in one launch (N = 2 ... 18000: CTA ranges that span
+    several chains and tiles, several staging windows per CTA, chains that
+    stop at different steps) and more chains than one launch takes (40 > 32:
+    two consecutive launches, a set with fewer units than CTAs), each against
+    the reparameterised oracle with the same shift."""
     mixed = np.concatenate([W.pixel(18000, 130.0, 30.0, 0.3, 0.5, 0.5), W.pixel(2, 10.0, 30.0, 3.0, 1.0, 1.0),
                             W.pixel(37, 75.0, 30.0, 2.0, 0.5, 0.5), W.pixel(333, 130.0, 50.0, 1.0, 3.0, 6.0),
                             W.pixel(2000, 75.0, 5.0, 1.0, 5.0, 0.01), W.pixel(1024, 95.0, 30.0, 0.5, 9.0, 9.0)])

@@ -70,37 +70,55 @@ def test_plan_rejects_bad_arguments():
             spl.chain_run_plan(*args)
 
 
-# ---------------------------------------------------------------- multi-chain groups
+# ---------------------------------------------------------------- multi-chain lockstep partition
+
+def _tile_contributors(n_bins, active, G):
+    """Largest number of CTAs one column tile of each active chain meets when
+    the units of the active chains, chain after chain, are split as
+    [b U / G', (b+1) U / G') over G' = min(G, U) CTAs (the kernel's partition)."""
+    T = [(n + 127) // 128 for n in n_bins]
+    RB = [spl.chain_run_plan(n, 1, 1)["vlen"] // 32 for n in n_bins]
+    U = sum(T[g] * RB[g] for g in active)
+    Ge = min(G, U)
+    owner = lambda u: ((u + 1) * Ge + U - 1) // U - 1
+    out, base = {}, 0
+    for g in active:
+        t = np.arange(T[g], dtype=np.int64)
+        first = base + t * RB[g]
+        last = first + RB[g] - 1
+        out[g] = int((owner(last) - owner(first) + 1).max())
+        base += T[g] * RB[g]
+    return out
+
 
 @pytest.mark.parametrize("n_bins,sms,bps", [
-    ([10000] * 12, 152, 2),                                   # the dead-time sweep: 25-26 CTAs each
-    ([18000, 2, 37, 333, 2000, 1024], 152, 2),                # one large chain and tiny ones (floor of 1 each)
-    (list(range(2, 700, 22)), 152, 2),                        # 32 small chains
-    ([5] * 32, 16, 2),                                        # 32 tiny chains on 32 resident CTAs: one each
+    ([10000] * 12, 152, 2),                                   # the dead-time sweep
+    ([18000, 2, 37, 333, 2000, 1024], 152, 2),                # one large chain and tiny ones
+    ([2, 5, 40, 130, 700], 152, 2),                           # fewer units than CTAs
     ([16000, 500], 4, 1),
 ])
-def test_chains_plan_invariants(n_bins, sms, bps):
-    G = spl.chains_plan(n_bins, sms, bps)
-    total = sms * bps
-    assert G.sum() <= total
-    for g, n in enumerate(n_bins):
-        cap = spl.chain_run_plan(n, sms, bps)["grid"]
-        assert 1 <= G[g] <= cap
-    # the whole GPU is used unless every chain is at its cap
-    caps = np.array([spl.chain_run_plan(n, sms, bps)["grid"] for n in n_bins])
-    assert G.sum() == min(total, caps.sum())
-    # equal sizes get equal shares to within one CTA
-    if len(set(n_bins)) == 1:
-        assert G.max() - G.min() <= 1
-    # more work never gets fewer CTAs (up to the rounding of one CTA)
-    order = np.argsort(n_bins)
-    assert np.all(np.diff(G[order]) >= -1)
+def test_chains_plan_slots_bound_every_step(n_bins, sms, bps):
+    """Whatever subset of the chains is still iterating, no tile meets more
+    CTAs than the partial slots the plan gives its chain."""
+    import itertools
+    slots = spl.chains_plan(n_bins, sms, bps)
+    G = sms * bps
+    n = len(n_bins)
+    subsets = [list(c) for r in range(1, n + 1) for c in itertools.combinations(range(n), r)]
+    if len(subsets) > 300:
+        rng = np.random.default_rng(5)
+        subsets = [subsets[i] for i in rng.choice(len(subsets), 300, replace=False)] + [list(range(n))] + \
+                  [[g] for g in range(n)]
+    for act in subsets:
+        for g, c in _tile_contributors(n_bins, act, G).items():
+            assert c <= slots[g], (act, g, c, slots[g])
+    assert np.all(slots >= 1) and np.all(slots <= G)
 
 
 def test_chains_plan_rejects_bad_arguments():
     with pytest.raises(spl.SplError):
         spl.chains_plan([100] * 33, 152, 2)       # more than one launch takes
     with pytest.raises(spl.SplError):
-        spl.chains_plan([100] * 5, 2, 2)          # more chains than resident CTAs
-    with pytest.raises(spl.SplError):
         spl.chains_plan([1, 100], 152, 2)         # a chain needs 2 bins
+    with pytest.raises(spl.SplError):
+        spl.chains_plan([100], 0, 2)
