@@ -740,6 +740,9 @@ struct BatchWorkspace {
     // copies of the host-buffer entry points overlap the next range's compute
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_range = nullptr;
+    // barrier words and set counters of the multi-chain launch
+    unsigned *multi_words = nullptr;
+    size_t multi_words_cap = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -1207,6 +1210,8 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
     cudaStream_t s = chains[0]->stream;
     cudaError_t e = grow(&ws->reps, &ws->reps_cap, (size_t)n);
     if (e != cudaSuccess) return status_of_alloc(e, "reports");
+    if ((e = grow(&ws->multi_words, &ws->multi_words_cap, (size_t)kMultiWords)) != cudaSuccess)
+        return status_of_alloc(e, "barrier words");
     const int bps = std::min(2, chain_multi_blocks_per_sm(chain_run_max_chunk()));
     if (bps < 1) return cuda_fail(cudaErrorLaunchOutOfResources, "multi-chain occupancy");
     const int grid = bps * num_sms_current();
@@ -1217,7 +1222,26 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
         const int m = std::min<int32_t>(kChainMultiMax, n - k0);
         std::memset(&M, 0, sizeof(M));
         M.n = m;
-        M.bar = chains[k0]->run_bar;
+        M.words = ws->multi_words;
+        // two CTA sets (one CTA of each SM in each) when there are two CTAs per
+        // SM and two chains or more: chains split in order into two runs of
+        // about equal work per pass (N^2)
+        M.nsets = (bps == 2 && m >= 2) ? 2 : 1;
+        M.set_begin[0] = 0;
+        M.set_begin[1] = m;
+        M.set_begin[2] = m;
+        if (M.nsets == 2) {
+            double W = 0.0, acc = 0.0;
+            for (int g = 0; g < m; ++g) W += (double)chains[k0 + g]->N * chains[k0 + g]->N;
+            int split = 1;
+            double best = INFINITY;
+            for (int q = 1; q < m; ++q) {
+                acc += (double)chains[k0 + q - 1]->N * chains[k0 + q - 1]->N;
+                const double worst = std::max(acc, W - acc);
+                if (worst < best) { best = worst; split = q; }
+            }
+            M.set_begin[1] = split;
+        }
         M.tol_err = (float)(0.5 * tol);
         M.min_iter = 1;
         M.max_iter = max_iter;

@@ -1247,13 +1247,15 @@ constexpr int kRunTW = 32 * kRunC;                      // columns per tile (one
 constexpr int kRunMaxChunk = 8192;                      // rows of v in shared memory at once
 constexpr unsigned kBarAbort = 0xFFFFFFFFu;
 constexpr int kBarGen = 32;                             // index of the generation word
+static_assert(3 * 2 * kBarGen <= kMultiCountWord, "three barriers before the set counters");
 constexpr uint32_t kGridSpinLimit = 1u << 24;
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
     unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void red_release_add_gpu(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -1268,8 +1270,9 @@ __device__ __forceinline__ int add_acq_rel_gpu(int *p, int v) {
     return old;
 }
 
-// Barrier over the G CTAs of one group of a cooperative launch (the whole
-// grid, or the CTAs that share one chain); b is the CTA's index in its group.
+// Barrier over the G CTAs of a cooperative launch; b is the CTA's index.
+// Waiting threads poll with relaxed loads and a short sleep, and acquire once
+// when the wait ends (an acquire at every poll slowed the other CTA of the SM).
 // bar[0] counts arrivals since launch, bar[kBarGen] (another 128-byte line)
 // is the released generation; gen is the calling CTA's count of barriers
 // passed (thread 0's copy is the one used).  False if the group was aborted.
@@ -1283,12 +1286,14 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err
         if (b == 0) {
             const unsigned target = next * (unsigned)G;
             uint32_t spins = 0;
-            while ((int)(ld_acquire_gpu(&bar[0]) - target) < 0) {
+            while ((int)(ld_relaxed_gpu(&bar[0]) - target) < 0) {
                 if (++spins > limit) {
                     ok = false;
                     break;
                 }
+                __nanosleep(32);
             }
+            fence_acq_rel_gpu();   // acquire the arrivals' writes once, not at every poll
             if (ok) {
                 ok = cas_release_gpu(&bar[kBarGen], gen, next) == gen;
             } else {
@@ -1298,14 +1303,16 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err
         } else {
             unsigned g;
             uint32_t spins = 0;
-            while ((g = ld_acquire_gpu(&bar[kBarGen])) == gen) {
+            while ((g = ld_relaxed_gpu(&bar[kBarGen])) == gen) {
                 if (++spins > limit) {
                     atomicExch(err_flag, 1);
                     atomicExch(&bar[kBarGen], kBarAbort);
                     g = kBarAbort;
                     break;
                 }
+                __nanosleep(32);
             }
+            fence_acq_rel_gpu();
             ok = g != kBarAbort;
         }
         gen = next;
@@ -1700,9 +1707,37 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     __shared__ int s_fin[kChainMultiMax];
     __shared__ int s_tile[6];                           // shared first / last tile: chain, tile, slots
     constexpr int kWinUnits = kRunMaxChunk / 32;
+    __shared__ int s_reg[2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x, n = m.n;
     unsigned gen = 0u;
+    // CTA sets: with two sets, the two CTAs of each SM go to different sets
+    // (each set runs its own chains in lockstep with its own barrier), so one
+    // CTA's barrier, normalisation and decisions overlap the other's FMA work
+    int G = gridDim.x, b = blockIdx.x, n = m.n;
+    const ChainRunArgs *cc = m.c;
+    unsigned *sbar = m.words;
+    if (m.nsets == 2) {
+        if (tid == 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            const unsigned slot = atomicAdd(m.words + kMultiSlotWord + smid % kMultiSmSlots, 1u);
+            s_reg[0] = (int)(slot & 1u);
+            s_reg[1] = (int)atomicAdd(m.words + kMultiCountWord + (slot & 1u), 1u);
+        }
+        unsigned gen0 = 0u;
+        // every CTA has registered before a set's size is read
+        if (!grid_sync(m.words, gen0, m.c[0].err_flag, &s_flag, blockIdx.x, gridDim.x)) {
+            if (tid < m.n) *m.c[tid].err_flag = 1;
+            return;
+        }
+        const int set = s_reg[0];
+        b = s_reg[1];
+        G = (int)__ldcg(m.words + kMultiCountWord + set);
+        cc = m.c + m.set_begin[set];
+        n = m.set_begin[set + 1] - m.set_begin[set];
+        sbar = m.words + (1 + set) * 2 * kBarGen;
+        if (n == 0) return;   // a set without chains: nothing waits for its CTAs
+    }
 
     // thread 0: unit and bin bases of the chains in `mask`, into slot sl
     auto bases = [&](int sl, unsigned mask) {
@@ -1711,8 +1746,8 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
             s_ub[sl][g] = u;
             s_nb[sl][g] = j;
             if (mask >> g & 1u) {
-                u += (long long)m.c[g].T * m.c[g].RB;
-                j += m.c[g].N;
+                u += (long long)cc[g].T * cc[g].RB;
+                j += cc[g].N;
             }
         }
         s_ub[sl][n] = u;
@@ -1756,7 +1791,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     // 16-byte async copies of a window's rows into buffer buf; step k reads
     // the start vector (k = 1) or the previous step's broadcast vector
     auto stage = [&](int g, long long lw0, long long lw1, int buf, int k) {
-        const ChainRunArgs &c = m.c[g];
+        const ChainRunArgs &c = cc[g];
         const float *src = k == 1 ? c.v0 : c.vb + (size_t)((k - 1) & 1) * c.vlen;
         const int RB = c.RB;
         const int off0 = (int)(lw0 % RB);
@@ -1771,9 +1806,9 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     };
 
     if (tid < n) {
-        s_st[tid] = m.c[tid].state->st;
+        s_st[tid] = cc[tid].state->st;
         s_inv[tid] = 1.f;
-        s_eL[tid] = (float)m.c[tid].scal[1];
+        s_eL[tid] = (float)cc[tid].scal[1];
     }
     if (tid == 0) bases(1, n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u));
     __syncthreads();
@@ -1795,12 +1830,12 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         int cur_g = -1, cur_t = -1;
         float mlo[kRunC], mhi[kRunC], acc[kRunC];
         auto flush = [&]() {
-            const ChainRunArgs &c = m.c[cur_g];
+            const ChainRunArgs &c = cc[cur_g];
             const long long tu = s_ub[sl][cur_g] + (long long)cur_t * c.RB;
             const int bf = (int)lk_owner(tu, U, Ge), bl = (int)lk_owner(tu + c.RB - 1, U, Ge);
             const int slot = b - bf;
             if (bf != bl && slot >= c.segs) {          // outside the partial slots: report, write nothing
-                if (tid == 0) atomicExch(m.c[0].err_flag, 1);
+                if (tid == 0) atomicExch(cc[0].err_flag, 1);
                 return;
             }
             lk_flush(c, cur_t, k, bf == bl, slot, acc, wred, s_inv[cur_g]);
@@ -1819,7 +1854,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const ChainRunArgs &c = m.c[g];
+            const ChainRunArgs &c = cc[g];
             const int RB = c.RB, N = c.N;
             const float *wbuf = sv + (size_t)(wi & 1) * m.chunk;
             for (int t = (int)(lw0 / RB); (long long)t * RB < lw1; ++t) {
@@ -1866,7 +1901,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
                 int prev_g = -1, prev_t = -1;
                 for (int e = 0; e < 2; ++e) {
                     const int q = chain_of(sl, ue[e]);
-                    const ChainRunArgs &c = m.c[q];
+                    const ChainRunArgs &c = cc[q];
                     const int t = (int)((ue[e] - s_ub[sl][q]) / c.RB);
                     if (q == prev_g && t == prev_t) break;
                     prev_g = q;
@@ -1890,13 +1925,13 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         }
         __syncthreads();
         const int lastmask = s_flag;
-        if (lastmask & 1) lk_tile_reduce(m.c[s_tile[0]], s_tile[1], k, s_tile[2]);
-        if (lastmask & 2) lk_tile_reduce(m.c[s_tile[3]], s_tile[4], k, s_tile[5]);
-        if (!grid_sync(m.bar, gen, m.c[0].err_flag, &s_flag, b, G)) {
+        if (lastmask & 1) lk_tile_reduce(cc[s_tile[0]], s_tile[1], k, s_tile[2]);
+        if (lastmask & 2) lk_tile_reduce(cc[s_tile[3]], s_tile[4], k, s_tile[5]);
+        if (!grid_sync(sbar, gen, cc[0].err_flag, &s_flag, b, G)) {
             if (tid < n) {
-                *m.c[tid].err_flag = 1;
+                *cc[tid].err_flag = 1;
                 if (b == 0) {
-                    ChainState *stp = m.c[tid].state;
+                    ChainState *stp = cc[tid].state;
                     stp->st = s_st[tid];
                     stp->done = 1;
                     stp->status = ST_ENOCONV;
@@ -1910,10 +1945,17 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         const int pk = (k + 2) % 3;
         for (int q = wid; q < n; q += kRunW) {
             if (!(mask >> q & 1u)) continue;
-            const ChainRunArgs &c = m.c[q];
+            const ChainRunArgs &c = cc[q];
             const float *ts = c.tsum + (size_t)(k & 1) * 4 * c.T;
+            const int nts = 4 * c.T;
             float sy = 0.f;
-            for (int i = lane; i < 4 * c.T; i += 32) sy += __ldcg(ts + i);
+            for (int i = lane; i < nts; i += 128) {   // four independent loads per lane in flight
+                const float x0 = __ldcg(ts + i);
+                const float x1 = i + 32 < nts ? __ldcg(ts + i + 32) : 0.f;
+                const float x2 = i + 64 < nts ? __ldcg(ts + i + 64) : 0.f;
+                const float x3 = i + 96 < nts ? __ldcg(ts + i + 96) : 0.f;
+                sy += (x0 + x1) + (x2 + x3);
+            }
             sy = warp_sum(sy);
             float sx = 0.f, sd = 0.f, s1 = 0.f, s2 = 0.f;
             if (k >= 2) {
@@ -1949,7 +1991,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         for (int q = 0; q < n; ++q)
             if ((mask >> q & 1u) && s_fin[q]) next &= ~(1u << q);
         if (b == 0 && tid < n && (mask >> tid & 1u) && s_fin[tid]) {
-            ChainState *stp = m.c[tid].state;
+            ChainState *stp = cc[tid].state;
             stp->st = s_st[tid];
             stp->done = 1;
             stp->status = s_fin[tid] == 1 ? ST_OK : ST_ENOCONV;
@@ -1975,7 +2017,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
                     if (!(mask >> q & 1u)) continue;
                     const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
                     if (cb1 <= j0 || cb0 >= j1) continue;
-                    const ChainRunArgs &c = m.c[q];
+                    const ChainRunArgs &c = cc[q];
                     const int a0 = (int)(max(j0, cb0) - cb0), a1 = (int)(min(j1, cb1) - cb0);
                     if (s_fin[q]) {
                         // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
@@ -2033,7 +2075,7 @@ __global__ void __launch_bounds__(kRunNT) chain_multi_init_kernel(const __grid_c
     }
     for (int t = tid; t < a.T; t += kRunNT) a.tile_ticket[t] = 0;
     if (blockIdx.x == 0)
-        for (int q = tid; q < 2 * kBarGen; q += kRunNT) m.bar[q] = 0u;
+        for (int q = tid; q < kMultiWords; q += kRunNT) m.words[q] = 0u;
     if (tid == 0) {
         *a.err_flag = 0;
         ChainState *stp = a.state;

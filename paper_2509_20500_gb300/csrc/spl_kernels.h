@@ -114,10 +114,18 @@ struct ChainMultiArgs {
     int64_t off[kChainMultiMax];
     int n;
     int chunk;               // rows per staging buffer
-    unsigned *bar;           // [chain_run_bar_words()] grid barrier words, zeroed by the start kernel
+    int nsets;               // 1: all CTAs run all chains; 2: two CTA sets, chains [set_begin[s], set_begin[s+1])
+    int set_begin[3];
+    unsigned *words;         // [kMultiWords] barrier words and set counters, zeroed by the start kernel
     float tol_err;
     int min_iter, max_iter;
 };
+// Layout of ChainMultiArgs::words: three barriers (the whole grid, set 0,
+// set 1) of 64 words each, two set sizes, one CTA counter per SM id.
+constexpr int kMultiCountWord = 192;
+constexpr int kMultiSlotWord = 194;
+constexpr int kMultiSmSlots = 1024;
+constexpr int kMultiWords = kMultiSlotWord + kMultiSmSlots;
 
 int chain_run_tile_cols();
 int chain_run_bar_words();
