@@ -403,6 +403,44 @@ def run_gpu(args):
                             "vs_plain_batch": plain_ms / na,
                             "what": "spl_batch_stationary_noalloc, uniform start, same 65536 pixels"}
 
+    # dense power steps with the row sums from the O(N) scans (one dense pass
+    # fewer per pixel): both arms, with the learned output audited
+    if not args.no_rowscan:
+        rs = {}
+        for arm in (("learned", "plain") if learned else ("plain",)):
+            def rs_step(arm=arm, time_kernel=False, reports=False):
+                if arm == "learned":
+                    return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off,
+                                                reports=reports, c_pixels=c_px, pass_kind=spl.SPL_PASS_DENSE_ROWSCAN,
+                                                time_kernel=time_kernel)
+                return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
+                                            c_pixels=c_px, time_kernel=time_kernel,
+                                            pass_kind=spl.SPL_PASS_DENSE_ROWSCAN)
+            _, _, rr = rs_step(reports=True)
+            assert np.all(rr["status"] == 0)
+            for _ in range(args.warmup):
+                rs_step()
+            rms, rkern = timed_steps(lambda: rs_step(time_kernel=True), args.steps, flush, stream,
+                                     spl.batch_kernel_ms)
+            rk = statistics.median(rkern)
+            rflop = float(2.0 * np.sum(N2 * rr["iters"]))
+            item = {"value": world * n / (statistics.mean(rms) / 1e3), "ms_per_step": statistics.mean(rms),
+                    "kernel_ms": rk, "iters_mean": float(rr["iters"].mean()),
+                    "roofline": {"bound": "alu", "achieved": rflop / (rk / 1e3) / 1e12, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": rflop / (rk / 1e3) / 1e12 / peak,
+                                 "work": "2 FLOP x N^2 x iters per pixel (power steps; row sums O(N))"}}
+            if arm == "learned" and not args.no_cpu_baseline and rank == 0:
+                import oracle
+                idx = W.sample_indices(n, args.audit, seed=91)
+                refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
+                o = out.cpu().numpy().astype(np.float64)
+                dif = [np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]) for r, k in enumerate(idx)]
+                item["accuracy_vs_oracle"] = {"sampled_pixels": len(idx), "max_l1": max(float(d.sum()) for d in dif),
+                                              "max_abs": max(float(d.max()) for d in dif)}
+            rs[arm] = item
+        rs["note"] = "SPL_PASS_DENSE_ROWSCAN: dense regenerated power steps, row sums by prefix/suffix scans"
+        extra["dense_rowscan"] = rs
+
     # the O(N) structured form of the same power step (reported beside the
     # dense path, never as its number): plain and learned starts
     if not args.no_structured:
@@ -763,6 +801,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
     ap.add_argument("--no-highres", action="store_true")
     ap.add_argument("--no-structured", action="store_true")
+    ap.add_argument("--no-rowscan", action="store_true")
     ap.add_argument("--no-noalloc", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-spectral", action="store_true")

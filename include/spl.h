@@ -152,6 +152,11 @@ typedef enum {
     SPL_PASS_STRUCTURED = 1,  /* the same step through the triangular structure of Eq. 6:
                                  y_j = w_j (P_j + e^-Lambda (T - P_j)) with P a prefix sum
                                  (O(N) per step; row sums by prefix and suffix scans) */
+    SPL_PASS_DENSE_ROWSCAN = 2, /* dense power steps as SPL_PASS_DENSE (N^2 FFMA per step), with the
+                                 row sums of P~'s normalisation taken from the same triangular
+                                 structure: r'_k = u_k (sum_{j>=k} w_j + e^-Lambda sum_{j<k} w_j), a
+                                 suffix and a prefix scan (O(N) once per pixel, instead of one more
+                                 dense pass) */
 } spl_pass_kind_t;
 
 /* Column weights of P~ (how the detection density enters bin j). */

@@ -970,7 +970,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                        cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0,
                        int tune = 0, int level_req = -1, int chunks = 1, const RangeFn *after_range = nullptr) {
     const int npad = batch_pad_len(nmax);
-    const bool st_kind = structured != 0;
+    const bool st_kind = structured == SPL_PASS_STRUCTURED;
     const int fault = injected_fault();
     if (fault == 1) return status_of_alloc(cudaErrorMemoryAllocation, "px (injected)");
     cudaError_t e;
@@ -993,7 +993,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     a.tol_err = (float)(0.5 * tol);
     a.max_iter = max_iter;
     a.min_iter = std::max(1, min_iter);
-    a.structured = structured;
+    a.structured = st_kind ? 1 : 0;
+    a.row_scan = structured == SPL_PASS_DENSE_ROWSCAN ? 1 : 0;
     a.flux_kind = flux_kind;
     a.pconst = ws.pconst;
 
@@ -1092,7 +1093,7 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     const int threads = opts ? opts->threads : 0;
     const bool timed = opts && opts->time_kernel;
     const int structured = opts ? opts->pass_kind : 0;
-    if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    if (structured < SPL_PASS_DENSE || structured > SPL_PASS_DENSE_ROWSCAN) return SPL_EINVAL;
     const int flux_kind = opts ? opts->flux_kind : 0;
     if (flux_kind != SPL_FLUX_POINT && flux_kind != SPL_FLUX_BININT) return SPL_EINVAL;
     const int tune = opts ? opts->tune : 0;
@@ -1129,7 +1130,7 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
     const int flux_kind = opts ? opts->flux_kind : 0;
     const int tune = opts ? opts->tune : 0;
     const int level = opts ? opts->state_level : -1;
-    if (structured != SPL_PASS_DENSE && structured != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    if (structured < SPL_PASS_DENSE || structured > SPL_PASS_DENSE_ROWSCAN) return SPL_EINVAL;
     if (flux_kind != SPL_FLUX_POINT && flux_kind != SPL_FLUX_BININT) return SPL_EINVAL;
     if (tune < 0 || tune > 2 || (tune == 2 && (level < 0 || level > 2))) return SPL_EINVAL;
     BatchWorkspace *ws = nullptr;
@@ -1343,7 +1344,7 @@ extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t 
 extern "C" spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_kind, int32_t *threads,
                                               int32_t *state_level, int32_t *blocks_per_sm) {
     if (n_bins_max < 2 || !threads || !state_level || !blocks_per_sm) return SPL_EINVAL;
-    if (pass_kind != SPL_PASS_DENSE && pass_kind != SPL_PASS_STRUCTURED) return SPL_EINVAL;
+    if (pass_kind < SPL_PASS_DENSE || pass_kind > SPL_PASS_DENSE_ROWSCAN) return SPL_EINVAL;
     const TuneKey key{batch_pad_len(n_bins_max), pass_kind, num_sms_current()};
     TuneVal v;
     if (!tune_lookup(key, &v)) return SPL_ENOCONV;

@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         __syncthreads();
 
         // ---- row sums r'_k, rho_k = u_k / r'_k
-        if constexpr (STRUCT) {
+        if (STRUCT || a.row_scan) {
             // r'_k / u_k = sum_{j >= k} w_j + eL sum_{j < k} w_j: an inclusive
             // suffix scan and an inclusive prefix scan of w (prefix - w_k is the
             // exclusive prefix, whose rounding is damped by eL).

@@ -47,6 +47,7 @@ struct BatchArgs {
     int max_iter;
     int min_iter;
     int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
+    int row_scan;            // 1 (dense steps): row sums by the scans of the structured form, not a dense pass
     int flux_kind;           // spl_flux_kind_t: 0 point flux (Sec. 3.4), 1 bin-integrated
     PixelConst *pconst;      // [n] per-pixel constants (work-list order), written by launch_batch
 };

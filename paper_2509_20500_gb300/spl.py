@@ -42,7 +42,7 @@ class spl_batch_opts_t(ctypes.Structure):
 
 
 SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
-SPL_PASS_DENSE, SPL_PASS_STRUCTURED = 0, 1
+SPL_PASS_DENSE, SPL_PASS_STRUCTURED, SPL_PASS_DENSE_ROWSCAN = 0, 1, 2
 SPL_FLUX_POINT, SPL_FLUX_BININT = 0, 1
 
 

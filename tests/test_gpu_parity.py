@@ -585,11 +585,14 @@ def test_batch_empty(spl):
 
 # ---------------------------------------------------------------- structured O(N) step
 
-def test_structured_step_array_sample_vs_oracle(spl):
-    """The O(N) scan form of the power step (y_j = w_j (P_j + e^-Lambda (T - P_j)))
-    on the 128x128 array: 64 sampled pixels against the FP64 oracle."""
+@pytest.mark.parametrize("kind", ["structured", "dense_rowscan"])
+def test_structured_step_array_sample_vs_oracle(spl, kind):
+    """The O(N) scan form of the power step (y_j = w_j (P_j + e^-Lambda (T - P_j))),
+    and the dense step with the row sums from the same scans, on the 128x128
+    array: 64 sampled pixels against the FP64 oracle."""
     px = W.array128()
-    out, off, reps = spl.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_STRUCTURED)
+    pk = spl.SPL_PASS_STRUCTURED if kind == "structured" else spl.SPL_PASS_DENSE_ROWSCAN
+    out, off, reps = spl.batch_stationary(px, tol=1e-6, pass_kind=pk)
     assert np.all(reps["status"] == 0)
     idx = W.sample_indices(len(px), 64, seed=34)
     refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
@@ -599,21 +602,25 @@ def test_structured_step_array_sample_vs_oracle(spl):
 
 
 def test_structured_and_dense_steps_agree_on_ragged_batch(spl):
-    """Both forms of the step reach the same pmf (each within 1e-6 L1 of the
-    oracle) on uneven sizes, including N above one scan tile (2048)."""
+    """Both forms of the step, and the dense step with scan row sums, reach
+    the same pmf (each within 1e-6 L1 of the oracle) on uneven sizes,
+    including N above one scan tile (2048)."""
     a = W.random_small(30, seed=18, n_min=2, n_max=400)
     b = W.uneven(16, seed=19)
     b = b[b["n_bins"] <= 8000]
     px = np.concatenate([a, b])
     d, off, rd = spl.batch_stationary(px, tol=1e-6)
     s, _, rs = spl.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_STRUCTURED)
-    assert np.all(rs["status"] == 0)
-    d, s = d.cpu().numpy(), s.cpu().numpy()
+    r, _, rr = spl.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_DENSE_ROWSCAN)
+    assert np.all(rs["status"] == 0) and np.all(rr["status"] == 0)
+    d, s, r = d.cpu().numpy(), s.cpu().numpy(), r.cpu().numpy()
     for k, p in enumerate(W.as_dicts(px)):
         assert _l1(d[off[k]:off[k + 1]], s[off[k]:off[k + 1]]) < L1_TOL, (k, p["n_bins"])
+        assert _l1(d[off[k]:off[k + 1]], r[off[k]:off[k + 1]]) < L1_TOL, (k, p["n_bins"])
         if p["n_bins"] <= 2000:
             ref = oracle.stationary(p, shift=oracle.shift_l(p))
-            assert _l1(s[off[k]:off[k + 1]], ref) < L1_TOL, (k, p)
+            _assert_pmf(s[off[k]:off[k + 1]], ref, (k, p))
+            _assert_pmf(r[off[k]:off[k + 1]], ref, (k, p, "rowscan"))
 
 
 def test_uneven_workload_full_batch(spl):
@@ -684,14 +691,15 @@ def test_spectral_statements_of_sec4_on_gpu(spl):
     assert np.all(res[95.0][3:, :, 1] < 0.2)
 
 
-@pytest.mark.parametrize("pass_kind", ["dense", "structured"])
+@pytest.mark.parametrize("pass_kind", ["dense", "structured", "dense_rowscan"])
 def test_every_launch_configuration_gives_the_same_pmfs(spl, pass_kind):
     """The state level only moves vectors between shared and global memory:
     every level the autotuner may pick gives the same pmfs bit for bit
     (ragged N up to 9000, which reaches every level).  512-thread blocks sum
     their reductions in another order: within the parity tolerance of the
     256-thread result."""
-    pk = spl.SPL_PASS_DENSE if pass_kind == "dense" else spl.SPL_PASS_STRUCTURED
+    pk = {"dense": spl.SPL_PASS_DENSE, "structured": spl.SPL_PASS_STRUCTURED,
+          "dense_rowscan": spl.SPL_PASS_DENSE_ROWSCAN}[pass_kind]
     px = np.concatenate([W.random_small(6, seed=71, n_min=20, n_max=300), W.array_pixels(3, seed=72),
                          W.pixel(9000, 40.0, 30.0, 0.3, 0.5, 0.5), W.pixel(4100, 130.0, 60.0, 0.8, 2.0, 1.0)])
     ref, off, _ = spl.batch_stationary(px, pass_kind=pk, tune=1)
@@ -706,7 +714,7 @@ def test_every_launch_configuration_gives_the_same_pmfs(spl, pass_kind):
         np.testing.assert_array_equal(o.cpu().numpy(), ref)
         seen += 1
     assert seen >= 2
-    if pass_kind == "dense":
+    if pass_kind != "structured":
         o, _, _ = spl.batch_stationary(px, pass_kind=pk, tune=2, threads=512, state_level=0)
         o = o.cpu().numpy().astype(np.float64)
         for k in range(len(px)):
