@@ -5,8 +5,9 @@ Workload (one step): the 256 x 256 pixel array (65536 pixels, N = 2000,
 t_r = 100 ns, t_d = 75 ns, tau ~ U[5,95] ns, sigma ~ U[0.2,1] ns,
 S, B ~ logU[0.01,5], seed 5).  A step runs the whole path through the C ABI:
 the warm-start network's forward pass on the tensor cores, the dead-time
-shift (host), FP64 cumulative flux, row sums and matrix-free power iteration
-of every pixel to the 1e-6 stop rule in one persistent launch.  The network
+shift (host), FP64 cumulative flux, row sums (O(N) prefix and suffix scans)
+and matrix-free power iteration of every pixel to the 1e-6 stop rule in one
+persistent launch, every step regenerating all N^2 entries of P~.  The network
 is trained first (untimed) on 200k pmfs the plain solver produces.  The plain
 arm (uniform start) is timed on the same workload and reported beside it.
 
@@ -282,9 +283,13 @@ def run_gpu(args):
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # the timed path: dense regenerated power steps (N^2 FFMA per step), the
+    # row sums of the normalisation from the O(N) scans of Eq. 6's structure
+    head_pass = spl.SPL_PASS_DENSE_ROWSCAN
+
     def plain_step(time_kernel=False, reports=False):
         return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
-                                    c_pixels=c_px, time_kernel=time_kernel)
+                                    c_pixels=c_px, time_kernel=time_kernel, pass_kind=head_pass)
 
     # ---- plain batched arm (uniform start)
     _, _, reps_plain = plain_step(reports=True)
@@ -307,7 +312,7 @@ def run_gpu(args):
 
         def learned_step(reports=False):
             return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
-                                        c_pixels=c_px)
+                                        c_pixels=c_px, pass_kind=head_pass)
 
         _, _, reps_l = learned_step(reports=True)
         assert np.all(reps_l["status"] == 0), "some pixels did not converge (learned start)"
@@ -335,10 +340,11 @@ def run_gpu(args):
     value = world * n / (ms / 1e3)
 
     # roofline of the dominant kernel: the persistent matrix-free batch kernel.
-    # Algorithmic work: every pixel runs one dense row pass and `iters` dense
-    # column passes over its N x N regenerated matrix, one FFMA (2 FLOP) per entry.
+    # Algorithmic work: every pixel runs `iters` dense column passes over its
+    # N x N regenerated matrix, one FFMA (2 FLOP) per entry (its row sums are
+    # O(N) scans).
     N2 = px["n_bins"].astype(np.float64) ** 2
-    flop = float(2.0 * np.sum(N2 * (1 + reps["iters"])))
+    flop = float(2.0 * np.sum(N2 * reps["iters"]))
     kms = statistics.median(kern_ms)
     achieved = flop / (kms / 1e3) / 1e12
     peak = fma["tflops_median"]
@@ -350,7 +356,8 @@ def run_gpu(args):
             "algorithmic_bytes": float(total * 4 * (2 if learned else 1) + n * 40),
             "bytes_basis": "pmf write (4 B per bin)" + (" + learned logits read (4 B per bin)" if learned else "")
                            + " + 40 B of parameters per pixel", "arm": arm,
-            "work": "2 FLOP x N^2 x (1 + iters) per pixel (row pass + power steps, one FFMA per entry)",
+            "work": "2 FLOP x N^2 x iters per pixel (dense power steps, one FFMA per regenerated entry; "
+                    "the row sums are O(N) scans)",
             "peak_basis": "of measured: spl_fp32_fma_peak (16 FMA chains per thread, 4 x 256 threads per SM, "
                           "median of 5 launches of ~50 ms) in this run",
             "peak_fp32_best_of_5": fma["tflops_best"], "sms": sms,
@@ -389,6 +396,44 @@ def run_gpu(args):
                       "iters_mean": float(reps_plain["iters"].mean()), "iters_max": int(reps_plain["iters"].max()),
                       "kernel_ms": statistics.median(plain_kern)}
 
+    # the same dense power steps with the row sums from one more dense pass
+    # (regenerating every entry of P~ for its row sums): both arms
+    if not args.no_rowpass:
+        rs = {}
+        for arm in (("learned", "plain") if learned else ("plain",)):
+            def rs_step(arm=arm, time_kernel=False, reports=False):
+                if arm == "learned":
+                    return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off,
+                                                reports=reports, c_pixels=c_px, pass_kind=spl.SPL_PASS_DENSE,
+                                                time_kernel=time_kernel)
+                return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
+                                            c_pixels=c_px, time_kernel=time_kernel,
+                                            pass_kind=spl.SPL_PASS_DENSE)
+            _, _, rr = rs_step(reports=True)
+            assert np.all(rr["status"] == 0)
+            for _ in range(args.warmup):
+                rs_step()
+            rms, rkern = timed_steps(lambda: rs_step(time_kernel=True), args.steps, flush, stream,
+                                     spl.batch_kernel_ms)
+            rk = statistics.median(rkern)
+            rflop = float(2.0 * np.sum(N2 * (1 + rr["iters"])))
+            item = {"value": world * n / (statistics.mean(rms) / 1e3), "ms_per_step": statistics.mean(rms),
+                    "kernel_ms": rk, "iters_mean": float(rr["iters"].mean()),
+                    "roofline": {"bound": "alu", "achieved": rflop / (rk / 1e3) / 1e12, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": rflop / (rk / 1e3) / 1e12 / peak,
+                                 "work": "2 FLOP x N^2 x (1 + iters) per pixel (dense row pass + power steps)"}}
+            if arm == "learned" and not args.no_cpu_baseline and rank == 0:
+                import oracle
+                idx = W.sample_indices(n, args.audit, seed=91)
+                refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
+                o = out.cpu().numpy().astype(np.float64)
+                dif = [np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]) for r, k in enumerate(idx)]
+                item["accuracy_vs_oracle"] = {"sampled_pixels": len(idx), "max_l1": max(float(d.sum()) for d in dif),
+                                              "max_abs": max(float(d.max()) for d in dif)}
+            rs[arm] = item
+        rs["note"] = "SPL_PASS_DENSE: the same power steps, row sums by a dense regenerating pass"
+        extra["dense_rowpass"] = rs
+
     # the allocation-free entry point on the same pixels (plain start): what
     # its fixed scratch and default launch shape cost against the plain arm
     if not args.no_noalloc:
@@ -400,46 +445,10 @@ def run_gpu(args):
         na_ms, _ = timed_steps(na_step, args.steps, flush, stream)
         na = statistics.mean(na_ms)
         extra["noalloc"] = {"value": world * n / (na / 1e3), "ms_per_step": na,
-                            "vs_plain_batch": plain_ms / na,
-                            "what": "spl_batch_stationary_noalloc, uniform start, same 65536 pixels"}
-
-    # dense power steps with the row sums from the O(N) scans (one dense pass
-    # fewer per pixel): both arms, with the learned output audited
-    if not args.no_rowscan:
-        rs = {}
-        for arm in (("learned", "plain") if learned else ("plain",)):
-            def rs_step(arm=arm, time_kernel=False, reports=False):
-                if arm == "learned":
-                    return net.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off,
-                                                reports=reports, c_pixels=c_px, pass_kind=spl.SPL_PASS_DENSE_ROWSCAN,
-                                                time_kernel=time_kernel)
-                return spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=reports,
-                                            c_pixels=c_px, time_kernel=time_kernel,
-                                            pass_kind=spl.SPL_PASS_DENSE_ROWSCAN)
-            _, _, rr = rs_step(reports=True)
-            assert np.all(rr["status"] == 0)
-            for _ in range(args.warmup):
-                rs_step()
-            rms, rkern = timed_steps(lambda: rs_step(time_kernel=True), args.steps, flush, stream,
-                                     spl.batch_kernel_ms)
-            rk = statistics.median(rkern)
-            rflop = float(2.0 * np.sum(N2 * rr["iters"]))
-            item = {"value": world * n / (statistics.mean(rms) / 1e3), "ms_per_step": statistics.mean(rms),
-                    "kernel_ms": rk, "iters_mean": float(rr["iters"].mean()),
-                    "roofline": {"bound": "alu", "achieved": rflop / (rk / 1e3) / 1e12, "peak": peak,
-                                 "unit": "TFLOP/s", "frac": rflop / (rk / 1e3) / 1e12 / peak,
-                                 "work": "2 FLOP x N^2 x iters per pixel (power steps; row sums O(N))"}}
-            if arm == "learned" and not args.no_cpu_baseline and rank == 0:
-                import oracle
-                idx = W.sample_indices(n, args.audit, seed=91)
-                refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
-                o = out.cpu().numpy().astype(np.float64)
-                dif = [np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]) for r, k in enumerate(idx)]
-                item["accuracy_vs_oracle"] = {"sampled_pixels": len(idx), "max_l1": max(float(d.sum()) for d in dif),
-                                              "max_abs": max(float(d.max()) for d in dif)}
-            rs[arm] = item
-        rs["note"] = "SPL_PASS_DENSE_ROWSCAN: dense regenerated power steps, row sums by prefix/suffix scans"
-        extra["dense_rowscan"] = rs
+                            "what": "spl_batch_stationary_noalloc (uniform start, dense row pass and steps), "
+                                    "same 65536 pixels"}
+        if "dense_rowpass" in extra:
+            extra["noalloc"]["vs_spl_batch_stationary_same_pass"] = extra["dense_rowpass"]["plain"]["ms_per_step"] / na
 
     # the O(N) structured form of the same power step (reported beside the
     # dense path, never as its number): plain and learned starts
@@ -674,7 +683,7 @@ def run_gpu(args):
         h_out = torch.empty(total, dtype=torch.float32).pin_memory()
         if learned:
             fn = (lambda: net.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_out, reports=False,
-                                                    c_pixels=c_px))
+                                                    c_pixels=c_px, pass_kind=head_pass))
         else:
             h_np = h_out.numpy()
             fn = (lambda: spl.batch_stationary_host(px, tol=TOL, max_iter=MAX_ITER, out=h_np, reports=False,
@@ -693,7 +702,9 @@ def run_gpu(args):
         if learned:
             learned_step()
         else:
-            plain_step()
+            # the plain host-buffer entry point takes no options: the dense row pass
+            spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=False,
+                                 c_pixels=c_px, pass_kind=spl.SPL_PASS_DENSE)
         torch.cuda.synchronize()
         e2e_same = bool(torch.equal(h_out, out.cpu()))
     h2d = n * 56
@@ -708,7 +719,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pixels_per_gpu": n, "n_bins": 2000, "tol_l1": TOL,
                    "path": ("learned warm start (tcgen05 MLP) + batched matrix-free power iteration" if learned
-                            else "plain batched (uniform start), matrix-free dense power step"),
+                            else "plain batched (uniform start), matrix-free dense power step")
+                           + "; every step regenerates all N^2 entries, row sums by O(N) scans",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}, pixels sharded, no collective"},
         "iters": {"mean": float(reps["iters"].mean()), "max": int(reps["iters"].max())},
@@ -801,7 +813,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="time the plain batched path only")
     ap.add_argument("--no-highres", action="store_true")
     ap.add_argument("--no-structured", action="store_true")
-    ap.add_argument("--no-rowscan", action="store_true")
+    ap.add_argument("--no-rowpass", action="store_true")
     ap.add_argument("--no-noalloc", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-spectral", action="store_true")

@@ -176,13 +176,16 @@ typedef struct {
     int32_t time_kernel;      /* 1: record CUDA events around the batch kernel (see spl_batch_kernel_ms) */
     int32_t pass_kind;        /* spl_pass_kind_t */
     int32_t flux_kind;        /* spl_flux_kind_t */
-    int32_t tune;             /* launch configuration: 0 (default) 256-thread blocks with the state level and
-                                 blocks per SM measured on the first batch of at least 1024 pixels of a kind
-                                 (padded n_bins, pass kind, SM count) and cached, also in the file
-                                 SPL_TUNE_CACHE names if set; these choices give the same pmfs bit for bit.
-                                 1 fixed heuristic; 2 explicit threads and state_level.  threads = 512 changes
-                                 the order of the block reductions (results within rounding, not bitwise). */
+    int32_t tune;             /* launch configuration: 0 (default) measured on the first batch of at least
+                                 1024 pixels of a kind (padded n_bins, pass kind, SM count) and cached, also in
+                                 the file SPL_TUNE_CACHE names if set: block size (256 or 512 threads) and
+                                 columns per thread (8 or 4; dense passes only), state level, blocks per SM.
+                                 1 fixed heuristic (256 threads, 8 columns); 2 explicit threads, state_level and
+                                 cols.  State level and blocks per SM leave the pmfs unchanged bit for bit; the
+                                 block size (order of the block reductions) and the columns per thread (where
+                                 the diagonal span splits each column's sum) change them within rounding. */
     int32_t state_level;      /* tune == 2: per-pixel vectors in shared memory (2 all, 1 three, 0 one) */
+    int32_t cols;             /* tune == 2, dense passes: columns per thread, 8 or 4 (0 = 8) */
 } spl_batch_opts_t;
 
 /* spl_batch_stationary with options (opts may be NULL for the defaults). */
@@ -229,10 +232,10 @@ SPL_API spl_status_t spl_mc_histograms(const spl_pixel_t *h_pixels, int32_t n, i
 
 /* The measured launch configuration cached for batches whose largest pixel
  * has n_bins_max bins and pass kind pass_kind on the current device:
- * SPL_OK with *threads, *state_level and *blocks_per_sm, or SPL_ENOCONV if
- * none is cached yet. */
+ * SPL_OK with *threads, *state_level, *blocks_per_sm and *cols (columns per
+ * thread; cols may be NULL), or SPL_ENOCONV if none is cached yet. */
 SPL_API spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_kind, int32_t *threads,
-                                           int32_t *state_level, int32_t *blocks_per_sm);
+                                           int32_t *state_level, int32_t *blocks_per_sm, int32_t *cols);
 
 /* Device time in ms of the batch kernel of the last spl_batch_stationary_ex
  * call on the current device that set time_kernel (events recorded on that

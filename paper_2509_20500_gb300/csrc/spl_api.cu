@@ -836,19 +836,23 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 
 struct LaunchCfg {
     int threads = 256, level = 2, bps = 0;   // bps: blocks per SM (at most the occupancy limit)
+    int cols = 8;                            // columns per thread of the dense passes (8 or 4)
     size_t smem = 0;
 };
 
-spl_status_t batch_cfg(int threads, int level, int npad, bool structured, LaunchCfg *cfg) {
+spl_status_t batch_cfg(int threads, int level, int npad, bool structured, LaunchCfg *cfg, int cols = 8) {
     if (threads != 256 && threads != 512) return SPL_EINVAL;
     if (structured && threads != 256) return SPL_EINVAL;
     if (level < 0 || level > 2) return SPL_EINVAL;
+    if (cols != 8 && cols != 4) return SPL_EINVAL;
+    if (structured && cols != 8) return SPL_EINVAL;
     cfg->threads = threads;
     cfg->level = level;
+    cfg->cols = cols;
     cfg->smem = batch_smem_bytes(npad, level);
     if (cfg->smem > 220 * 1024) return SPL_EINVAL;
     int bps = 0;
-    SPL_CU(batch_occupancy(threads, level, structured, cfg->smem, &bps));
+    SPL_CU(batch_occupancy(threads, level, structured, cfg->smem, &bps, cols));
     if (bps < 1) return SPL_EINVAL;
     cfg->bps = bps;
     return SPL_OK;
@@ -866,8 +870,8 @@ int injected_fault() {
     return 0;
 }
 
-using TuneKey = std::array<int, 3>;      // padded N, structured, SMs
-using TuneVal = std::array<int, 3>;      // threads, state level, blocks per SM
+using TuneKey = std::array<int, 3>;      // padded N, pass kind, SMs
+using TuneVal = std::array<int, 4>;      // threads, state level, blocks per SM, columns per thread
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 bool g_tune_loaded = false;
@@ -879,9 +883,16 @@ void tune_load_locked() {
     const char *path = std::getenv("SPL_TUNE_CACHE");
     if (!path || !*path) return;
     if (FILE *f = std::fopen(path, "r")) {
-        int v[6];
-        while (std::fscanf(f, "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6)
-            g_tune[TuneKey{v[0], v[1], v[2]}] = TuneVal{v[3], v[4], v[5]};
+        // one entry per line: key (padded N, pass kind, SMs), then threads,
+        // state level, blocks per SM and (optional, default 8) columns per thread
+        char line[256];
+        while (std::fgets(line, sizeof(line), f)) {
+            int v[7];
+            const int got = std::sscanf(line, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]);
+            if (got == 6) v[6] = 8;
+            else if (got != 7) break;   // a line broken off: the rest of the file is ignored
+            g_tune[TuneKey{v[0], v[1], v[2]}] = TuneVal{v[3], v[4], v[5], v[6]};
+        }
         std::fclose(f);
     }
 }
@@ -891,7 +902,7 @@ void tune_store_locked(const TuneKey &k, const TuneVal &v) {
     const char *path = std::getenv("SPL_TUNE_CACHE");
     if (!path || !*path) return;
     if (FILE *f = std::fopen(path, "a")) {
-        std::fprintf(f, "%d %d %d %d %d %d\n", k[0], k[1], k[2], v[0], v[1], v[2]);
+        std::fprintf(f, "%d %d %d %d %d %d %d\n", k[0], k[1], k[2], v[0], v[1], v[2], v[3]);
         std::fclose(f);
     }
 }
@@ -921,12 +932,16 @@ spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, i
     a.n = n;
     a.scratch = ws.scratch;
     a.state_level = cfg.level;
+    a.cols = cfg.cols;
     SPL_CU(launch_batch(a, cfg.threads, grid, cfg.smem, s));
     return SPL_OK;
 }
 
 // Times every feasible configuration on a sample of the work list and keeps
-// the fastest (per pixel).
+// the fastest (per pixel).  State level and blocks per SM leave the pmfs
+// unchanged bit for bit; the block size (the order of the block reductions)
+// and the columns per thread (where the diagonal span cuts each column's sum
+// into chunks) change them within rounding.
 spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int npad, bool structured,
                         cudaStream_t s, LaunchCfg *best) {
     const int sms = num_sms_current();
@@ -934,9 +949,14 @@ spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int n
     if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
     if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
     float best_ms = INFINITY;
+    // block size and columns per thread (dense passes only), state level, and
+    // blocks per SM at the occupancy limit or one below
+    const int nthr = structured ? 1 : 2, ncol = structured ? 1 : 2;
+    for (int ti = 0; ti < nthr; ++ti)
+    for (int ci = 0; ci < ncol; ++ci)
     for (int level = 2; level >= 0; --level) {
         LaunchCfg top;
-        if (batch_cfg(256, level, npad, structured, &top) != SPL_OK) continue;
+        if (batch_cfg(ti ? 512 : 256, level, npad, structured, &top, ci ? 4 : 8) != SPL_OK) continue;
         for (int bps = top.bps; bps >= std::max(1, top.bps - 1); --bps) {
             LaunchCfg cfg = top;
             cfg.bps = bps;
@@ -968,7 +988,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
                        cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0,
-                       int tune = 0, int level_req = -1, int chunks = 1, const RangeFn *after_range = nullptr) {
+                       int tune = 0, int level_req = -1, int chunks = 1, const RangeFn *after_range = nullptr,
+                       int cols_req = 0) {
     const int npad = batch_pad_len(nmax);
     const bool st_kind = structured == SPL_PASS_STRUCTURED;
     const int fault = injected_fault();
@@ -1002,7 +1023,8 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
     spl_status_t st;
     if (tune == 2 || threads_req > 0) {
         const int level = level_req >= 0 ? level_req : batch_state_level(npad, st_kind);
-        if ((st = batch_cfg(threads_req > 0 ? threads_req : 256, level, npad, st_kind, &cfg)) != SPL_OK)
+        if ((st = batch_cfg(threads_req > 0 ? threads_req : 256, level, npad, st_kind, &cfg,
+                            cols_req > 0 ? cols_req : 8)) != SPL_OK)
             return st;
     } else {
         // heuristic: 256 threads, the largest state level that keeps three
@@ -1014,7 +1036,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
             const TuneKey key{npad, structured, num_sms_current()};
             TuneVal v;
             LaunchCfg c2;
-            if (tune_lookup(key, &v) && v[0] == 256 && batch_cfg(v[0], v[1], npad, st_kind, &c2) == SPL_OK &&
+            if (tune_lookup(key, &v) && batch_cfg(v[0], v[1], npad, st_kind, &c2, v[3]) == SPL_OK &&
                 v[2] >= 1 && v[2] <= c2.bps) {
                 c2.bps = v[2];
                 cfg = c2;
@@ -1023,7 +1045,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                 cfg = c2;
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 tune_load_locked();
-                tune_store_locked(key, TuneVal{cfg.threads, cfg.level, cfg.bps});
+                tune_store_locked(key, TuneVal{cfg.threads, cfg.level, cfg.bps, cfg.cols});
             }
         }
     }
@@ -1099,8 +1121,10 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     const int tune = opts ? opts->tune : 0;
     const int level = opts ? opts->state_level : -1;
     if (tune < 0 || tune > 2 || (tune == 2 && (level < 0 || level > 2))) return SPL_EINVAL;
+    const int cols = opts ? opts->cols : 0;
+    if (cols != 0 && cols != 4 && cols != 8) return SPL_EINVAL;
     st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed,
-                   structured, flux_kind, tune, tune == 2 ? level : -1);
+                   structured, flux_kind, tune, tune == 2 ? level : -1, 1, nullptr, cols);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the
@@ -1174,7 +1198,8 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
         return SPL_OK;
     };
     st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, warm_kind, warm_ld, min_iter, threads, d_out, nullptr, s,
-                   false, structured, flux_kind, tune, tune == 2 ? level : -1, uniform ? 4 : 1, &copy_range);
+                   false, structured, flux_kind, tune, tune == 2 ? level : -1, uniform ? 4 : 1, &copy_range,
+                   opts ? opts->cols : 0);
     if (st != SPL_OK) {
         cudaStreamSynchronize(cs);
         return st;
@@ -1342,7 +1367,7 @@ extern "C" spl_status_t spl_batch_spectral(const spl_pixel_t *h_pixels, int32_t 
 }
 
 extern "C" spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_kind, int32_t *threads,
-                                              int32_t *state_level, int32_t *blocks_per_sm) {
+                                              int32_t *state_level, int32_t *blocks_per_sm, int32_t *cols) {
     if (n_bins_max < 2 || !threads || !state_level || !blocks_per_sm) return SPL_EINVAL;
     if (pass_kind < SPL_PASS_DENSE || pass_kind > SPL_PASS_DENSE_ROWSCAN) return SPL_EINVAL;
     const TuneKey key{batch_pad_len(n_bins_max), pass_kind, num_sms_current()};
@@ -1351,6 +1376,7 @@ extern "C" spl_status_t spl_batch_tune_lookup(int32_t n_bins_max, int32_t pass_k
     *threads = v[0];
     *state_level = v[1];
     *blocks_per_sm = v[2];
+    if (cols) *cols = v[3];
     return SPL_OK;
 }
 

@@ -664,8 +664,12 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
                         mlo[c] = w;
                         mhi[c] = w * eL;
                     }
-                    // one code path for both chunk lengths (only the outer step differs)
-                    tri_pass<C, false>(sv, 0, nrow, base, lane, mlo, mhi, y, fine ? kChain : kChainCoarse);
+                    // one code path for both chunk lengths (only the outer step differs);
+                    // h is zero from N on, so a warp whose columns end below N stops at
+                    // N rounded up to 4 (the same sums bit for bit); the warp whose span
+                    // holds column N runs to the 32-row block boundary its span needs
+                    const int bhi = base + 32 * C <= N ? ((N + 3) & ~3) : nrow;
+                    tri_pass<C, false>(sv, 0, bhi, base, lane, mlo, mhi, y, fine ? kChain : kChainCoarse);
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
                         const int j = base + 32 * c + lane;
@@ -2377,20 +2381,30 @@ __global__ void __launch_bounds__(NT) finish_rows_kernel(int N, int nparts, int 
 
 int batch_threads_for(int nmax) { (void)nmax; return 256; }
 
-template <int NT, int LEVEL, bool STRUCT>
+template <int NT, int C, int LEVEL, bool STRUCT>
 static cudaError_t launch_batch_one(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
-    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL, STRUCT>;
+    auto k = batch_fused_kernel<NT, C, LEVEL, STRUCT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int NT, int C, bool STRUCT>
+static cudaError_t launch_batch_c(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
+    if (a.state_level == 2) return launch_batch_one<NT, C, 2, STRUCT>(a, grid, smem, s);
+    if (a.state_level == 1) return launch_batch_one<NT, C, 1, STRUCT>(a, grid, smem, s);
+    return launch_batch_one<NT, C, 0, STRUCT>(a, grid, smem, s);
+}
+
+// Dense passes with 8 (default) or 4 columns per thread; the structured step
+// has no column pass and runs with 8.
 template <int NT, bool STRUCT>
 static cudaError_t launch_batch_nt(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
-    if (a.state_level == 2) return launch_batch_one<NT, 2, STRUCT>(a, grid, smem, s);
-    if (a.state_level == 1) return launch_batch_one<NT, 1, STRUCT>(a, grid, smem, s);
-    return launch_batch_one<NT, 0, STRUCT>(a, grid, smem, s);
+    if constexpr (!STRUCT) {
+        if (a.cols == 4) return launch_batch_c<NT, 4, STRUCT>(a, grid, smem, s);
+    }
+    return launch_batch_c<NT, SPL_BATCH_C, STRUCT>(a, grid, smem, s);
 }
 
 cudaError_t launch_pixel_const(const PixelDev *px, int n, PixelConst *out, cudaStream_t s) {
@@ -2407,25 +2421,28 @@ cudaError_t launch_batch(const BatchArgs &a, int threads, int grid, size_t smem,
     return launch_batch_nt<256, false>(a, grid, smem, s);
 }
 
-template <int NT, int LEVEL, bool STRUCT>
+template <int NT, int C, int LEVEL, bool STRUCT>
 static cudaError_t occupancy_one(size_t smem, int *bps) {
-    auto k = batch_fused_kernel<NT, SPL_BATCH_C, LEVEL, STRUCT>;
+    auto k = batch_fused_kernel<NT, C, LEVEL, STRUCT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, smem);
 }
 
-template <int NT, bool STRUCT>
+template <int NT, int C, bool STRUCT>
 static cudaError_t occupancy_nt(int level, size_t smem, int *bps) {
-    if (level == 2) return occupancy_one<NT, 2, STRUCT>(smem, bps);
-    if (level == 1) return occupancy_one<NT, 1, STRUCT>(smem, bps);
-    return occupancy_one<NT, 0, STRUCT>(smem, bps);
+    if (level == 2) return occupancy_one<NT, C, 2, STRUCT>(smem, bps);
+    if (level == 1) return occupancy_one<NT, C, 1, STRUCT>(smem, bps);
+    return occupancy_one<NT, C, 0, STRUCT>(smem, bps);
 }
 
-cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm) {
-    if (structured) return occupancy_nt<256, true>(level, smem, blocks_per_sm);
-    if (threads == 512) return occupancy_nt<512, false>(level, smem, blocks_per_sm);
-    return occupancy_nt<256, false>(level, smem, blocks_per_sm);
+cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm, int cols) {
+    if (structured) return occupancy_nt<256, SPL_BATCH_C, true>(level, smem, blocks_per_sm);
+    if (threads == 512)
+        return cols == 4 ? occupancy_nt<512, 4, false>(level, smem, blocks_per_sm)
+                         : occupancy_nt<512, SPL_BATCH_C, false>(level, smem, blocks_per_sm);
+    return cols == 4 ? occupancy_nt<256, 4, false>(level, smem, blocks_per_sm)
+                     : occupancy_nt<256, SPL_BATCH_C, false>(level, smem, blocks_per_sm);
 }
 
 int batch_pad_len(int n) { return pad_len(n, SPL_BATCH_C); }

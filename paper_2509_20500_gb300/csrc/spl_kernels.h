@@ -48,6 +48,7 @@ struct BatchArgs {
     int min_iter;
     int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
     int row_scan;            // 1 (dense steps): row sums by the scans of the structured form, not a dense pass
+    int cols;                // columns per thread of the dense passes: 4, or 8 (any other value)
     int flux_kind;           // spl_flux_kind_t: 0 point flux (Sec. 3.4), 1 bin-integrated
     PixelConst *pconst;      // [n] per-pixel constants (work-list order), written by launch_batch
 };
@@ -192,7 +193,7 @@ int batch_threads_for(int nmax);
 size_t batch_smem_bytes(int npad, int level);
 int batch_state_level(int npad, bool structured);
 int batch_pad_len(int n);
-cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm);
+cudaError_t batch_occupancy(int threads, int level, bool structured, size_t smem, int *blocks_per_sm, int cols = 8);
 // The per-pixel constants of a work list (one thread per pixel); launch_batch
 // and launch_spectral run it before their kernels.
 cudaError_t launch_pixel_const(const PixelDev *px, int n, PixelConst *out, cudaStream_t s);

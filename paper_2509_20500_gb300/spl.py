@@ -38,7 +38,8 @@ class spl_report_t(ctypes.Structure):
 class spl_batch_opts_t(ctypes.Structure):
     _fields_ = [("warm_kind", ctypes.c_int32), ("warm_ld", ctypes.c_int32), ("min_iter", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("time_kernel", ctypes.c_int32), ("pass_kind", ctypes.c_int32),
-                ("flux_kind", ctypes.c_int32), ("tune", ctypes.c_int32), ("state_level", ctypes.c_int32)]
+                ("flux_kind", ctypes.c_int32), ("tune", ctypes.c_int32), ("state_level", ctypes.c_int32),
+                ("cols", ctypes.c_int32)]
 
 
 SPL_WARM_WEIGHTS, SPL_WARM_LOGITS, SPL_WARM_LEARNED = 0, 1, 2
@@ -133,6 +134,7 @@ def lib():
         L.spl_mlp_time_forward.argtypes = [vp, P, i32, i32, fp]
         L.spl_mlp_time_forward.restype = ctypes.c_int
         L.spl_batch_tune_lookup.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]
         L.spl_batch_tune_lookup.restype = ctypes.c_int
         L.spl_mlp_loss_grad.argtypes = [vp, P, i32, vp, fp, vp]
@@ -336,7 +338,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
                      warm_kind: int = SPL_WARM_WEIGHTS, warm_ld: int = 0, min_iter: int = 1, threads: int = 0,
                      reports: bool = True, offsets=None, stream=None, time_kernel: bool = False, c_pixels=None,
                      pass_kind: int = SPL_PASS_DENSE, flux_kind: int = SPL_FLUX_POINT, tune: int = 0,
-                     state_level: int = -1):
+                     state_level: int = -1, cols: int = 0):
     """spl_batch_stationary_ex over a PIXEL_DTYPE array; returns (out, offsets, reports)."""
     import torch
     px = np.ascontiguousarray(px, dtype=workloads.PIXEL_DTYPE)
@@ -349,7 +351,7 @@ def batch_stationary(px: np.ndarray, tol: float = 1e-6, max_iter: int = 1000, wa
     arr = pixels_to_c(px) if c_pixels is None else c_pixels
     reps = (spl_report_t * max(1, n))() if reports else None
     opts = spl_batch_opts_t(int(warm_kind), int(warm_ld), int(min_iter), int(threads), int(bool(time_kernel)),
-                            int(pass_kind), int(flux_kind), int(tune), int(state_level))
+                            int(pass_kind), int(flux_kind), int(tune), int(state_level), int(cols))
     st = lib().spl_batch_stationary_ex(arr, n, float(tol), int(max_iter), _dptr(warm), _dptr(out), _dptr(offsets),
                                        reps, _stream_ptr(stream), ctypes.byref(opts))
     _check(st, "spl_batch_stationary", (SPL_OK, SPL_ENOCONV))
@@ -380,15 +382,15 @@ def batch_stationary_noalloc(px: np.ndarray, tol: float = 1e-6, max_iter: int = 
 
 def batch_tune_lookup(n_bins_max: int, pass_kind: int = SPL_PASS_DENSE):
     """The cached measured launch configuration (threads, state level, blocks
-    per SM) for batches of this size and pass kind on the current device, or
-    None."""
-    t, lv, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    per SM, columns per thread) for batches of this size and pass kind on the
+    current device, or None."""
+    t, lv, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     st = lib().spl_batch_tune_lookup(int(n_bins_max), int(pass_kind), ctypes.byref(t), ctypes.byref(lv),
-                                     ctypes.byref(b))
+                                     ctypes.byref(b), ctypes.byref(c))
     if st == SPL_ENOCONV:
         return None
     _check(st, "spl_batch_tune_lookup")
-    return int(t.value), int(lv.value), int(b.value)
+    return int(t.value), int(lv.value), int(b.value), int(c.value)
 
 
 def mc_histograms(px: np.ndarray, runs: int, cycles: int, seed: int, out=None, stream=None):
@@ -568,7 +570,7 @@ class MLP:
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
         opts = spl_batch_opts_t(0, 0, 1, int(threads), int(bool(time_kernel)), int(pass_kind), int(flux_kind),
-                                int(tune), int(state_level))
+                                int(tune), int(state_level), 0)
         st = lib().spl_batch_stationary_learned(self._m, arr, n, float(tol), int(max_iter), _dptr(out),
                                                 _dptr(offsets), reps, self._stream, ctypes.byref(opts))
         _check(st, "spl_batch_stationary_learned", (SPL_OK, SPL_ENOCONV))
@@ -586,7 +588,7 @@ class MLP:
             out = torch.empty(int(off[-1]), dtype=torch.float32).pin_memory()
         reps = (spl_report_t * max(1, n))() if reports else None
         arr = pixels_to_c(px) if c_pixels is None else c_pixels
-        opts = spl_batch_opts_t(0, 0, 1, 0, 0, int(pass_kind), int(flux_kind), int(tune), -1)
+        opts = spl_batch_opts_t(0, 0, 1, 0, 0, int(pass_kind), int(flux_kind), int(tune), -1, 0)
         st = lib().spl_batch_stationary_learned_host(self._m, arr, n, float(tol), int(max_iter),
                                                      ctypes.c_void_p(out.data_ptr()), reps, self._stream,
                                                      ctypes.byref(opts))

@@ -35,10 +35,22 @@ def test_exports_every_declared_symbol(S):
     assert sorted(S.EXPORTED) == decl
 
 
-def test_struct_layouts(S):
+def test_struct_layouts(S, tmp_path):
+    """The binding's structures have the sizes the C header gives them (a
+    small C program compiled against include/spl.h prints them)."""
+    import subprocess
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "spl.h"\nint main(void) { printf("%zu %zu %zu %zu\\n", '
+                   'sizeof(spl_pixel_t), sizeof(spl_report_t), sizeof(spl_batch_opts_t), sizeof(spl_run_plan_t)); '
+                   'return 0; }\n')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(S.spl_pixel_t), ctypes.sizeof(S.spl_report_t), ctypes.sizeof(S.spl_batch_opts_t),
+                     ctypes.sizeof(S.spl_run_plan_t)]
     assert ctypes.sizeof(S.spl_pixel_t) == 56 == W.PIXEL_DTYPE.itemsize
     assert ctypes.sizeof(S.spl_report_t) == 24 == S.REPORT_DTYPE.itemsize
-    assert ctypes.sizeof(S.spl_batch_opts_t) == 36
+    assert ctypes.sizeof(S.spl_batch_opts_t) == 40
 
 
 def test_strerror_and_version(S):

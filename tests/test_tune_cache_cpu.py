@@ -1,7 +1,8 @@
 """The launch-configuration cache file (SPL_TUNE_CACHE) read back on the host:
-each line is "padded-N pass-kind SMs threads state-level blocks-per-SM";
-lookups find the entry of their batch kind and nothing else, and a file that
-breaks off mid-line keeps the entries before it.  No GPU: without a device
+each line is "padded-N pass-kind SMs threads state-level blocks-per-SM
+[columns-per-thread]" (8 columns when the last field is absent); lookups find
+the entry of their batch kind and nothing else, and a file that breaks off
+mid-line keeps the entries before it.  No GPU: without a device
 the library's SM count is 1, which the keys below use."""
 import os
 import subprocess
@@ -27,19 +28,19 @@ def _lookup(path):
 def test_cache_file_entries_are_found_by_kind(tmp_path):
     # padded lengths: 2000 -> 2048, 700 -> 768 (multiples of 256 for 8 columns per thread)
     f = tmp_path / "tune.txt"
-    f.write_text("2048 0 1 256 2 2\n2048 1 1 256 1 3\n768 0 1 256 0 1\n")
+    f.write_text("2048 0 1 256 2 2\n2048 1 1 256 1 3 8\n768 0 1 512 0 1 4\n")
     dense, structured, small, big = _lookup(f)
-    assert dense == [256, 2, 2]
-    assert structured == [256, 1, 3]
-    assert small == [256, 0, 1]
+    assert dense == [256, 2, 2, 8]          # a line without the column count: 8
+    assert structured == [256, 1, 3, 8]
+    assert small == [512, 0, 1, 4]
     assert big is None                      # nothing cached for that size
 
 
 def test_cache_file_broken_off_keeps_earlier_entries(tmp_path):
     f = tmp_path / "tune.txt"
-    f.write_text("2048 0 1 256 2 2\n768 0 1 2")   # the second line breaks off
+    f.write_text("2048 0 1 256 2 2 4\n768 0 1 2")   # the second line breaks off
     dense, structured, small, big = _lookup(f)
-    assert dense == [256, 2, 2] and structured is None and small is None
+    assert dense == [256, 2, 2, 4] and structured is None and small is None
 
 
 def test_missing_cache_file_means_nothing_cached(tmp_path):
