@@ -300,6 +300,14 @@ def run_gpu(args):
     plain_ms_list, plain_kern = timed_steps(lambda: plain_step(time_kernel=True), args.steps, flush, stream,
                                             spl.batch_kernel_ms)
     plain_ms = sum(plain_ms_list) / len(plain_ms_list)
+    # the autotuner's pick for this batch kind, and the fixed heuristic (tune=1) timed beside it
+    tcfg = spl.batch_tune_lookup(2000, head_pass)
+    spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off, reports=False, c_pixels=c_px,
+                         pass_kind=head_pass, tune=1)
+    _, dflt_kern = timed_steps(lambda: spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, out=out, offsets=d_off,
+                                                            reports=False, c_pixels=c_px, pass_kind=head_pass,
+                                                            tune=1, time_kernel=True),
+                               max(2, args.steps // 2), flush, stream, spl.batch_kernel_ms)
 
     # ---- learned warm start: trained (untimed) on pmfs the method generates
     learned = not args.no_learned
@@ -392,6 +400,12 @@ def run_gpu(args):
                                              "frac": mlp_flop / (mlp_ms / 1e3) / 1e12 / tpeak,
                                              "ms": mlp_ms, "peak_basis": "MEASURED_PEAKS bf16_tflops (burst), of measured",
                                              "work": "2 x 65536 x (5 x 512 + 3 x 512^2 + 512 x 2000) FLOP (real, unpadded sizes)"}}
+    extra["autotune_array256"] = {
+        "picked": dict(zip(("threads", "state_level", "blocks_per_sm", "cols"), tcfg)) if tcfg else None,
+        "plain_kernel_ms": statistics.median(plain_kern), "default_kernel_ms": statistics.median(dflt_kern),
+        "gain_over_default": statistics.median(dflt_kern) / statistics.median(plain_kern),
+        "searched": "threads {256, 512} x columns per thread {8, 4} x state level {2, 1, 0} x blocks per SM "
+                    "{occupancy limit, one below}, on 12 x SMs pixels of the first batch of the kind"}
     extra["plain"] = {"value": world * n / (plain_ms / 1e3), "ms_per_step": plain_ms,
                       "iters_mean": float(reps_plain["iters"].mean()), "iters_max": int(reps_plain["iters"].max()),
                       "kernel_ms": statistics.median(plain_kern)}
@@ -478,7 +492,8 @@ def run_gpu(args):
         st["note"] = "O(N) scan form of the power step (Eq. 6 triangular structure); same pmfs, not the dense-path number"
         extra["structured"] = st
 
-    # uneven workload: 4096 pixels, N in {500..16000}, one persistent launch
+    # uneven workload: 4096 pixels, N in {500..16000}, one persistent launch;
+    # the measured launch configuration against the fixed heuristic (tune=1)
     if not args.no_uneven and rank == 0:
         ux = W.uneven()
         ucp = spl.pixels_to_c(ux)
@@ -486,21 +501,32 @@ def run_gpu(args):
         uout = torch.empty(int(uoff[-1]), dtype=torch.float32, device=dev)
         udo = torch.from_numpy(uoff).to(dev)
         un = {}
-        for name, pk in (("dense", spl.SPL_PASS_DENSE), ("structured", spl.SPL_PASS_STRUCTURED)):
+        for name, pk in (("dense", head_pass), ("structured", spl.SPL_PASS_STRUCTURED)):
             _, _, ur = spl.batch_stationary(ux, tol=TOL, max_iter=MAX_ITER, out=uout, offsets=udo, c_pixels=ucp,
                                             pass_kind=pk)
             assert np.all(ur["status"] == 0)
-            fn = (lambda pk=pk: spl.batch_stationary(ux, tol=TOL, max_iter=MAX_ITER, out=uout, offsets=udo,
-                                                     c_pixels=ucp, reports=False, time_kernel=True, pass_kind=pk))
+            def fn(pk=pk, tune=0):
+                return spl.batch_stationary(ux, tol=TOL, max_iter=MAX_ITER, out=uout, offsets=udo, c_pixels=ucp,
+                                            reports=False, time_kernel=True, pass_kind=pk, tune=tune)
             fn()
             ums, ukern = timed_steps(fn, max(2, args.steps // 2), flush, stream, spl.batch_kernel_ms)
             item = {"value": len(ux) / (statistics.mean(ums) / 1e3), "ms_per_step": statistics.mean(ums),
                     "kernel_ms": statistics.median(ukern), "iters_mean": float(ur["iters"].mean()),
                     "iters_max": int(ur["iters"].max())}
-            if pk == spl.SPL_PASS_DENSE:
-                uf = float(2.0 * np.sum(ux["n_bins"].astype(np.float64) ** 2 * (1 + ur["iters"])))
+            if pk == head_pass:
+                uf = float(2.0 * np.sum(ux["n_bins"].astype(np.float64) ** 2 * ur["iters"]))
                 ua = uf / (item["kernel_ms"] / 1e3) / 1e12
-                item["roofline"] = {"bound": "alu", "achieved": ua, "peak": peak, "unit": "TFLOP/s", "frac": ua / peak}
+                item["roofline"] = {"bound": "alu", "achieved": ua, "peak": peak, "unit": "TFLOP/s", "frac": ua / peak,
+                                    "work": "2 FLOP x N^2 x iters per pixel"}
+                fn(tune=1)
+                _, dkern = timed_steps(lambda: fn(tune=1), max(2, args.steps // 2), flush, stream, spl.batch_kernel_ms)
+                cfg = spl.batch_tune_lookup(int(ux["n_bins"].max()), head_pass)
+                item["autotune"] = {"picked": dict(zip(("threads", "state_level", "blocks_per_sm", "cols"), cfg))
+                                    if cfg else None,
+                                    "default_kernel_ms": statistics.median(dkern),
+                                    "gain_over_default": statistics.median(dkern) / item["kernel_ms"],
+                                    "default": "256 threads, 8 columns per thread, largest state level that fits, "
+                                               "occupancy-limit blocks per SM"}
             un[name] = item
         un["workload"] = "uneven: 4096 pixels, N~U{500,...,16000}, t_d~U[20,150], tau=30, sigma=0.3, B=0.5, S~U{0.05,0.5,5}, seed 4"
         extra["uneven_4096"] = un

@@ -290,7 +290,7 @@ SPL_API spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels, i
 
 /*
  * Learned warm start (the paper has no network; this follows its batched use
- * case).  A 5 -> 4 x 512 (GELU) -> 2000 MLP, BF16 weights with FP32
+ * case).  A 5 -> 4 x 512 (GELU, tanh form) -> 2000 MLP, BF16 weights with FP32
  * accumulation on the tensor cores, maps (sub-bin pulse position, sigma,
  * log S, log B, x_d / t_r) of an n_bins = 2000 pixel to a log-correction of
  * the flux prior lambda(s_j) in a frame rolled to the pulse bin; its softmax

@@ -9,7 +9,8 @@ iteration.  Inputs (scaled to about [-1, 1]):
   f2 = (log S + 1.5) / 3.1
   f3 = (log B + 1.5) / 3.1
   f4 = 2 (t_d mod t_r) / t_r - 1
-Layers: 4 hidden layers h = GELU(W h + b) with GELU(x) = x Phi(x), then
+Layers: 4 hidden layers h = GELU(W h + b) with GELU in its tanh form
+x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (an approximation of x Phi(x)), then
 z = W h + b with one output per bin of the learned frame.  Output index i
 corresponds to bin (i + c) mod N; the start vector is
   q_j = softmax_j( z_{(j - c) mod N} + log lambda(s_j) )
@@ -27,7 +28,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy import special
 
 
 def features(p) -> tuple[np.ndarray, int]:
@@ -53,12 +53,20 @@ def log_prior(p) -> np.ndarray:
     return np.log(lam)
 
 
+GELU_K = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
+
+
 def gelu(x):
-    return x * special.ndtr(x)
+    """GELU in its tanh form (Hendrycks and Gimpel, 2016):
+    x/2 (1 + tanh(k (x + a x^3))), k = sqrt(2/pi), a = 0.044715; within 5e-4
+    of x Phi(x) everywhere."""
+    return 0.5 * x * (1.0 + np.tanh(GELU_K * (x + GELU_A * x ** 3)))
 
 
 def gelu_grad(x):
-    return special.ndtr(x) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    t = np.tanh(GELU_K * (x + GELU_A * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_K * (1.0 + 3.0 * GELU_A * x * x)
 
 
 def init_params(sizes, seed):

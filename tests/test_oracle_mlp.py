@@ -75,3 +75,17 @@ def test_loss_is_minimised_by_the_target():
         # loss(q0 | t) >= entropy(t), loss(q0 | q0) = entropy(q0)
         assert l_t >= -float(t @ np.log(t)) - 1e-12
     assert abs(l_at + float(q0 @ np.log(q0))) < 1e-12
+
+
+def test_gelu_tanh_form_against_x_phi_and_its_derivative():
+    """The activation is the tanh form of GELU: within 5e-4 of x Phi(x)
+    (Phi from math.erfc) on [-8, 8], odd part x/2 exactly (GELU(x) - GELU(-x)
+    = x), and its derivative matches central differences."""
+    import math
+    x = np.linspace(-8.0, 8.0, 4001)
+    exact = x * 0.5 * np.array([math.erfc(-v / math.sqrt(2.0)) for v in x])
+    assert np.abs(mlp.gelu(x) - exact).max() < 5e-4
+    np.testing.assert_allclose(mlp.gelu(x) - mlp.gelu(-x), x, rtol=0, atol=1e-12)
+    h = 1e-5
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    np.testing.assert_allclose(mlp.gelu_grad(x), fd, rtol=0, atol=1e-8)
