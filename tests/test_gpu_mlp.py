@@ -154,9 +154,12 @@ def test_learned_start_with_structured_step(spl):
 
 def test_headline_launch_array256_learned_sampled(spl):
     """The launch the benchmark times: the 256 x 256 array (65536 pixels,
-    N = 2000) with the learned start in one persistent launch, the launch
+    N = 2000) with the learned start in one persistent launch, dense steps
+    with the row sums from the scans (SPL_PASS_DENSE_ROWSCAN), the launch
     configuration chosen by the autotuner; 32 pixels sampled by seed against
-    the FP64 oracle, every pmf normalised, every pixel converged."""
+    the FP64 oracle (L1 and max-abs), every pmf normalised, every pixel
+    converged; the dense-row-pass form on the same network within the
+    tolerance of it."""
     train = W.training(16384, seed=2)
     tgt, _, _ = spl.batch_stationary(train, tol=1e-6)
     tgt = tgt.view(len(train), 2000)
@@ -168,15 +171,21 @@ def test_headline_launch_array256_learned_sampled(spl):
             net.train_step(cpx, 4096, tgt[b * 4096:(b + 1) * 4096], lr=3e-3 * min(1.0, (step + 1) / 20))
             step += 1
     px = W.array256()
-    out, off, reps = net.batch_stationary(px, tol=1e-6)
+    out, off, reps = net.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_DENSE_ROWSCAN)
     assert np.all(reps["status"] == 0)
     o = out.cpu().numpy().astype(np.float64)
     sums = np.add.reduceat(o, off[:-1])
     assert np.abs(sums - 1).max() < 1e-5
     idx = W.sample_indices(len(px), 32, seed=34)
     refs, roff, _, _ = oracle.batch_stationary(W.as_dicts(px[idx]), tol=1e-12)
-    worst = max(np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]).sum() for r, k in enumerate(idx))
-    assert worst < 1e-6, worst
+    dif = [np.abs(o[off[k]:off[k + 1]] - refs[roff[r]:roff[r + 1]]) for r, k in enumerate(idx)]
+    worst = max(d.sum() for d in dif)
+    assert worst < 1e-6 and max(d.max() for d in dif) <= worst, worst
+    d2, _, r2 = net.batch_stationary(px, tol=1e-6, pass_kind=spl.SPL_PASS_DENSE)
+    assert np.all(r2["status"] == 0)
+    d2 = d2.cpu().numpy().astype(np.float64)
+    for k in idx:
+        assert np.abs(d2[off[k]:off[k + 1]] - o[off[k]:off[k + 1]]).sum() < 1e-6
     net.close()
 
 
@@ -226,8 +235,9 @@ def test_learned_host_entry_point_matches_device_path(spl):
     for b in range(4):
         net.train_step(spl.pixels_to_c(train[b * 1024:(b + 1) * 1024]), 1024, tgt[b * 1024:(b + 1) * 1024], lr=2e-3)
     px = W.array_pixels(8192, seed=79)           # at least 16 x SMs pixels: four ranges
-    d, off, rd = net.batch_stationary(px, tol=1e-6)
-    h, off2, rh = net.batch_stationary_host(px, tol=1e-6)
+    pk = spl.SPL_PASS_DENSE_ROWSCAN              # the timed path's pass kind
+    d, off, rd = net.batch_stationary(px, tol=1e-6, pass_kind=pk)
+    h, off2, rh = net.batch_stationary_host(px, tol=1e-6, pass_kind=pk)
     assert np.array_equal(off, off2)
     np.testing.assert_array_equal(h.numpy(), d.cpu().numpy())
     for k in ("iters", "status", "last_step_l1"):

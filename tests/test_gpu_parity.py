@@ -324,6 +324,17 @@ def test_tune_cache_file_is_read(tmp_path):
     np.testing.assert_array_equal(np.load(tmp_path / "a.npy"), np.load(tmp_path / "b.npy"))
 
 
+def test_fp32_fma_peak_is_measured(spl):
+    """spl_fp32_fma_peak (the FP32 roofline denominator): the device's SM
+    count, and a rate between half the nominal peak at the maximum clock
+    and 5 % above it (nothing removed the FMAs)."""
+    r = spl.fp32_fma_peak(iters=100_000, reps=3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["sms"] == sms
+    nominal = sms * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal < r["tflops_median"] <= r["tflops_best"] * 1.0000001 < 1.05 * nominal, (r, nominal)
+
+
 def test_bounded_waits_give_up_and_context_stays_usable(spl):
     """The device-side waits give up after their limit: an mbarrier phase
     nothing completes and a grid barrier one CTA never reaches end with the
