@@ -1250,29 +1250,48 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
         M.n = m;
         M.words = ws->multi_words;
         // two CTA sets (one CTA of each SM in each) when there are two CTAs per
-        // SM and two chains or more: chains split in order into two runs of
-        // about equal work per pass (N^2)
+        // SM and two chains or more.  The chains are dealt to the sets one by
+        // one, in order, each to the set whose work per pass (N^2) stays the
+        // smaller relative to its share kSet0Share : 1 - kSet0Share, so that
+        // neighbouring chains (often similar ones) land in different sets.  The
+        // first CTA to start on an SM (set 0) gets the larger share of the
+        // SM's issue slots while both run (measured: with equal work, set 0
+        // finished its steps in 0.73 of set 1's time), so it takes more work.
+        constexpr double kSet0Share = 0.58;
         M.nsets = (bps == 2 && m >= 2) ? 2 : 1;
-        M.set_begin[0] = 0;
-        M.set_begin[1] = m;
-        M.set_begin[2] = m;
+        int order[kChainMultiMax];
+        int n0 = m;
         if (M.nsets == 2) {
-            double W = 0.0, acc = 0.0;
-            for (int g = 0; g < m; ++g) W += (double)chains[k0 + g]->N * chains[k0 + g]->N;
-            int split = 1;
-            double best = INFINITY;
-            for (int q = 1; q < m; ++q) {
-                acc += (double)chains[k0 + q - 1]->N * chains[k0 + q - 1]->N;
-                const double worst = std::max(acc, W - acc);
-                if (worst < best) { best = worst; split = q; }
+            int list[2][kChainMultiMax], cnt[2] = {0, 0};
+            double load[2] = {0.0, 0.0};
+            const double share[2] = {kSet0Share, 1.0 - kSet0Share};
+            for (int g = 0; g < m; ++g) {
+                const double w = (double)chains[k0 + g]->N * chains[k0 + g]->N;
+                const int q = (load[0] + w) / share[0] <= (load[1] + w) / share[1] ? 0 : 1;
+                load[q] += w;
+                list[q][cnt[q]++] = g;
             }
-            M.set_begin[1] = split;
+            if (cnt[1] == 0) list[1][cnt[1]++] = list[0][--cnt[0]];   // every set gets a chain
+            n0 = cnt[0];
+            for (int q = 0; q < cnt[0]; ++q) order[q] = list[0][q];
+            for (int q = 0; q < cnt[1]; ++q) order[n0 + q] = list[1][q];
+        } else {
+            for (int g = 0; g < m; ++g) order[g] = g;
         }
+        M.set_begin[0] = 0;
+        M.set_begin[1] = n0;
+        M.set_begin[2] = m;
         M.tol_err = (float)(0.5 * tol);
         M.min_iter = 1;
         M.max_iter = max_iter;
-        long long U = 0;
+        int64_t coff[kChainMultiMax];   // packed output offset of each chain, in the caller's order
         for (int g = 0; g < m; ++g) {
+            coff[g] = off;
+            off += chains[k0 + g]->N;
+        }
+        long long U = 0;
+        for (int q = 0; q < m; ++q) {
+            const int g = order[q];
             spl_chain *c = chains[k0 + g];
             U += (long long)c->run_T * c->run_RB;
             const int slots = chain_multi_slots(c->N, grid);
@@ -1298,9 +1317,9 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
             }
             ChainRunArgs a = run_args(c);
             a.segs = slots;
-            M.c[g] = a;
-            M.off[g] = off;
-            off += c->N;
+            M.c[q] = a;
+            M.off[q] = coff[g];
+            M.idx[q] = g;
         }
         // rows of one staging buffer: a window is at most chain_run_max_chunk()
         // rows and at most one CTA's share of the first step's units

@@ -2112,7 +2112,7 @@ __global__ void __launch_bounds__(kRunNT) chain_multi_finish_kernel(const __grid
         r.err_bound = h.st.err;
         r.lambda2_abs = h.st.rho;
         r.lambda2_phase = h.st.theta;
-        reps[blockIdx.x] = r;
+        reps[m.idx[blockIdx.x]] = r;
     }
 }
 

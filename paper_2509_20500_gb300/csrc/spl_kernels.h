@@ -104,16 +104,20 @@ struct ChainRunArgs {
 };
 
 // Several fused chains in one cooperative launch (at most kChainMultiMax),
-// in lockstep: at every power step the work units of the chains still
-// iterating are numbered one chain after the other and split evenly over all
-// CTAs (and their bins likewise for the normalisation), so a chain that
-// stops leaves no CTA idle.  c[g].segs is the number of partial slots per
-// column tile of chain g; c[g].blk holds [2][grid][4] statistics; c[g].bar is
-// unused (the launch has one barrier, bar).  Results go to out + off[g].
+// in lockstep: the CTAs form nsets sets (with two, one CTA of each SM in
+// each), set s runs chains [set_begin[s], set_begin[s+1]), and at every power
+// step the work units of its chains still iterating are numbered one chain
+// after the other and split evenly over the set's CTAs (their bins likewise
+// for the normalisation), so a chain that stops leaves no CTA idle.
+// c[g].segs is the number of partial slots per column tile of chain g;
+// c[g].blk holds [2][grid][4] statistics; c[g].bar is unused (the launch's
+// barriers are in words).  Results go to out + off[g], reports to
+// reps[idx[g]].
 constexpr int kChainMultiMax = 32;
 struct ChainMultiArgs {
     ChainRunArgs c[kChainMultiMax];
     int64_t off[kChainMultiMax];
+    int idx[kChainMultiMax];  // caller's position of chain g in this launch (its report slot)
     int n;
     int chunk;               // rows per staging buffer
     int nsets;               // 1: all CTAs run all chains; 2: two CTA sets, chains [set_begin[s], set_begin[s+1])

@@ -235,6 +235,30 @@ def test_chains_multi_launch_mixed_sizes_and_many_chains(spl):
             _assert_pmf(o[off[k]:off[k + 1]], ref, (k, pix[k]["n_bins"], reps[k]))
 
 
+def test_chains_multi_launch_max_iter_and_single_chain(spl):
+    """max_iter reached: every chain reports SPL_ENOCONV after exactly
+    max_iter steps and the call returns that status; a set of one chain runs
+    as one lockstep set and gives the single-chain kernel's pmf within the
+    tolerance and its step count within one."""
+    px = np.concatenate([W.pixel(3000, 75.0, 30.0, 0.5, 5.0, 0.5), W.pixel(1200, 40.0, 60.0, 0.8, 0.5, 0.05)])
+    cs = spl.ChainSet(px)
+    import ctypes
+    reps = (spl.spl_report_t * 2)()
+    out = torch.empty(int(cs.off[-1]), dtype=torch.float32, device="cuda")
+    st = spl.lib().spl_chains_stationary(cs._arr, 2, 1e-9, 2, ctypes.c_void_p(out.data_ptr()), reps)
+    assert st == spl.SPL_ENOCONV
+    assert [reps[k].iters for k in range(2)] == [2, 2]
+    assert [reps[k].status for k in range(2)] == [spl.SPL_ENOCONV] * 2
+    cs.close()
+    one = W.pixel(5000, 130.0, 30.0, 0.3, 0.5, 0.5)
+    m, _, rm = spl.chains_stationary(one, tol=1e-6)
+    ch = spl.Chain(one, spl.SPL_FUSED)
+    s1, r1 = ch.stationary(tol=1e-6)
+    ch.close()
+    assert rm["status"][0] == 0 and abs(int(rm["iters"][0]) - int(r1["iters"])) <= 1
+    assert _l1(m.cpu().numpy(), s1.cpu().numpy()) < L1_TOL
+
+
 def test_chains_multi_launch_rejects_bad_sets(spl):
     import ctypes
     L = spl.lib()
