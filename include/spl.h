@@ -403,8 +403,8 @@ SPL_API spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t blo
 /* Self-test of the device-side bounded waits, for tests: an mbarrier phase
  * that nothing completes (the wait gives up after a short limit), and a grid
  * barrier of a three-CTA cooperative launch that one CTA never reaches (the
- * polling CTA gives up, sets the error flag and writes the abort generation,
- * and the other waiting CTA leaves on it).  No fault, trap or hang is
+ * two waiting CTAs give up after the limit, set the error flag and poison the
+ * arrival count, which would release any other waiter).  No fault, trap or hang is
  * involved.  SPL_OK if every wait gave up as designed, SPL_EINVAL if one did
  * not, SPL_ECUDA on a CUDA error.
  *

@@ -1461,8 +1461,8 @@ extern "C" spl_status_t spl_selftest_bounded_waits(void *stream) {
     if (bar) cudaFree(bar);
     if (flags) cudaFree(flags);
     if (e != cudaSuccess) return note_cuda_error(e, "bounded-wait self-test");
-    // the mbarrier wait gave up; the polling CTA gave up and set the error
-    // flag; both CTAs that reached the grid barrier left it on the abort
+    // the mbarrier wait gave up; both CTAs that reached the grid barrier gave
+    // up, set the error flag and left it as aborted
     return (h[0] == 1 && h[1] == 1 && h[2] == 2) ? SPL_OK : SPL_EINVAL;
 }
 

@@ -1239,18 +1239,16 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
 //   decide      on step k-1: every CTA adds the statistics of step k-1 in CTA
 //               order and runs the stop rule on the same numbers, so all CTAs
 //               stop together; pi^(k-1) is then the result.
-// The barrier is a counter of arrivals since launch that one CTA polls before
-// it releases the next generation; every wait is bounded: a CTA that gives up
-// sets err_flag and an abort generation that releases every other waiter,
-// and all CTAs return.
+// The barrier is a counter of arrivals since launch that every CTA polls;
+// every wait is bounded: a CTA that gives up sets err_flag and poisons the
+// count, which releases every other waiter, and all CTAs return.
 
 constexpr int kRunNT = 256;
 constexpr int kRunW = kRunNT / 32;
 constexpr int kRunC = 4;
 constexpr int kRunTW = 32 * kRunC;                      // columns per tile (one warp span)
 constexpr int kRunMaxChunk = 8192;                      // rows of v in shared memory at once
-constexpr unsigned kBarAbort = 0xFFFFFFFFu;
-constexpr int kBarGen = 32;                             // index of the generation word
+constexpr int kBarGen = 32;                             // a barrier's slot is 2 kBarGen words (its own lines)
 static_assert(3 * 2 * kBarGen <= kMultiCountWord, "three barriers before the set counters");
 constexpr uint32_t kGridSpinLimit = 1u << 24;
 
@@ -1274,52 +1272,41 @@ __device__ __forceinline__ int add_acq_rel_gpu(int *p, int v) {
     return old;
 }
 
-// Barrier over the G CTAs of a cooperative launch; b is the CTA's index.
-// Waiting threads poll with relaxed loads and a short sleep, and acquire once
-// when the wait ends (an acquire at every poll slowed the other CTA of the SM).
-// bar[0] counts arrivals since launch, bar[kBarGen] (another 128-byte line)
-// is the released generation; gen is the calling CTA's count of barriers
-// passed (thread 0's copy is the one used).  False if the group was aborted.
+// Barrier over the G CTAs of a cooperative launch (b, the CTA's index, is
+// kept for the callers' symmetry).  bar[0] counts arrivals since launch; every
+// CTA adds one (release) and polls, with relaxed loads and a short sleep, until
+// the count reaches (gen + 1) G, then acquires once (fence.acq_rel).  gen is
+// the calling CTA's count of barriers passed (thread 0's copy is the one
+// used).  A CTA that gives up after `limit` polls sets err_flag and adds
+// kBarPoison, which releases every other waiter; a count at or above
+// kBarPoison means the grid was aborted (false).
+constexpr unsigned kBarPoison = 0x40000000u;
+
 __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *err_flag, int *s_flag, int b,
                                           int G, uint32_t limit = kGridSpinLimit) {
+    (void)b;
     __syncthreads();
     if (threadIdx.x == 0) {
-        bool ok = true;
-        const unsigned next = gen + 1u;
+        const unsigned target = (gen + 1u) * (unsigned)G;
         red_release_add_gpu(&bar[0], 1u);
-        if (b == 0) {
-            const unsigned target = next * (unsigned)G;
-            uint32_t spins = 0;
-            while ((int)(ld_relaxed_gpu(&bar[0]) - target) < 0) {
-                if (++spins > limit) {
-                    ok = false;
-                    break;
-                }
-                __nanosleep(32);
+        uint32_t spins = 0;
+        unsigned v;
+        bool ok = true;
+        while ((v = ld_relaxed_gpu(&bar[0])) < target) {
+            if (++spins > limit) {
+                ok = false;
+                break;
             }
-            fence_acq_rel_gpu();   // acquire the arrivals' writes once, not at every poll
-            if (ok) {
-                ok = cas_release_gpu(&bar[kBarGen], gen, next) == gen;
-            } else {
-                atomicExch(err_flag, 1);
-                atomicExch(&bar[kBarGen], kBarAbort);
-            }
-        } else {
-            unsigned g;
-            uint32_t spins = 0;
-            while ((g = ld_relaxed_gpu(&bar[kBarGen])) == gen) {
-                if (++spins > limit) {
-                    atomicExch(err_flag, 1);
-                    atomicExch(&bar[kBarGen], kBarAbort);
-                    g = kBarAbort;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            fence_acq_rel_gpu();
-            ok = g != kBarAbort;
+            __nanosleep(32);
         }
-        gen = next;
+        fence_acq_rel_gpu();   // acquire the arrivals' writes once, not at every poll
+        if (!ok) {
+            atomicExch(err_flag, 1);
+            atomicAdd(&bar[0], kBarPoison);
+        } else if (v >= kBarPoison) {
+            ok = false;
+        }
+        gen += 1u;
         *s_flag = ok ? 1 : 0;
     }
     __syncthreads();
@@ -2123,8 +2110,8 @@ __global__ void __launch_bounds__(kRunNT) chain_multi_finish_kernel(const __grid
 // The waits of the kernels above give up after a limit and report; these two
 // kernels make such waits run out on purpose, with short limits: an mbarrier
 // phase that nothing completes, and a grid barrier that one CTA of a
-// cooperative launch never reaches (the polling CTA gives up and writes the
-// abort generation, which releases the other waiting CTA).
+// cooperative launch never reaches (both waiting CTAs give up, set the error
+// flag and poison the arrival count).
 
 __global__ void selftest_mbar_kernel(int *status, uint32_t limit) {
     __shared__ __align__(8) uint64_t bar;

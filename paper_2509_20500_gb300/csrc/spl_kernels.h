@@ -151,8 +151,8 @@ cudaError_t launch_chain_multi(const ChainMultiArgs &m, int grid, float *out, Re
 int chain_multi_slots(int n_bins, int grid);
 int chain_multi_blocks_per_sm(int chunk);
 // Waits that run out on purpose (status[0]: the mbarrier wait gave up;
-// status[1]: CTAs that left the grid barrier on the abort; err_flag set by the
-// CTA that gave up).  bar: chain_run_bar_words() zeroed words.
+// status[1]: CTAs that left the grid barrier as aborted; err_flag set by the
+// CTAs that gave up).  bar: chain_run_bar_words() zeroed words.
 cudaError_t launch_selftest_waits(unsigned *bar, int *err_flag, int *status, cudaStream_t s);
 
 // FP32 FMA throughput kernel on `sms` SMs: fma_peak_flop() FLOP per launch,
