@@ -1405,7 +1405,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
     extern __shared__ float4 smem4[];
     float *sv = reinterpret_cast<float *>(smem4);
     __shared__ float wred[kRunW][kRunTW];
-    __shared__ float red[5 * kRunW + 5];
+    __shared__ float red[9 * kRunW];                 // [0, 5 W) and [5 W, 9 W): the two step sums
     __shared__ int s_flag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int N = a.N, T = a.T, RB = a.RB;
@@ -1561,7 +1561,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             f1 = a.d1[jf];
             f2 = a.d2[jf];
         }
-        block_sum_k<kRunNT, 5>(red5, red);
+        block_sum_k_1bar<kRunNT, 5>(red5, red);
         inv = 1.f / red5[4];
         if (tid == 0) {
             int fin = 0;
@@ -1595,7 +1595,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             a.d1[j] = d;
             pcur[j] = pn;
         }
-        block_sum_k<kRunNT, 4>(stats, red);   // its barriers also publish s_flag
+        block_sum_k_1bar<kRunNT, 4>(stats, red + 5 * kRunW);   // its barrier also publishes s_flag
         if (s_flag) {
             // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
             if ((k - 1) & 1)
@@ -1687,7 +1687,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     extern __shared__ float4 smem4[];
     float *sv = reinterpret_cast<float *>(smem4);
     __shared__ float wred[kRunW][kRunTW];
-    __shared__ float red[5 * kRunW + 5];
+    __shared__ float red[8 * kRunW];                 // two alternating buffers of the per-chain sums
     __shared__ int s_flag;
     __shared__ long long s_ub[3][kChainMultiMax + 1];   // unit bases of the chains in step k's pass: slot k % 3
     __shared__ long long s_nb[3][kChainMultiMax + 1];   // bin bases (the normalisation of step k)
@@ -2004,6 +2004,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
             const int GeN = (int)min((long long)G, NB);
             if (b < GeN) {
                 const long long j0 = (long long)b * NB / GeN, j1 = (long long)(b + 1) * NB / GeN;
+                int piece = 0;
                 for (int q = 0; q < n; ++q) {
                     if (!(mask >> q & 1u)) continue;
                     const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
@@ -2034,7 +2035,9 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
                         c.d1[j] = d;
                         pcur[j] = pn;
                     }
-                    block_sum_k<kRunNT, 4>(stats, red);
+                    // one barrier; consecutive chains alternate buffers, so a buffer
+                    // is rewritten only after every thread passed the barrier between
+                    block_sum_k_1bar<kRunNT, 4>(stats, red + (piece++ & 1) * 4 * kRunW);
                     if (tid == 0)
                         reinterpret_cast<float4 *>(c.blk + (size_t)(k & 1) * G * 4)[b] =
                             make_float4(stats[0], stats[1], stats[2], stats[3]);
