@@ -754,7 +754,8 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "host-buffer entry point (copy-back overlapped with compute in four ranges)",
+                "path": "host-buffer entry point (one launch; each of eight ranges copied back as soon as the kernel "
+                        "has finished it)",
                 "same_pmfs_as_device_path": e2e_same},
     }
     line.update(extra)

@@ -247,10 +247,11 @@ SPL_API spl_status_t spl_batch_kernel_ms(float *ms);
  * Same computation as spl_batch_stationary with HOST buffers: h_warm (NULL or
  * packed host floats), h_out (packed host floats, offsets from the n_bins of
  * h_pixels in order) and h_reports (may be NULL).  Copies inputs to the device
- * and results back inside the call; synchronises `stream`.  A batch of one
- * size runs as four consecutive ranges of at least four waves each, and each
- * range's results are copied back on a library-owned stream while the next
- * range computes (same pmfs bit for bit as one launch).
+ * and results back inside the call; synchronises `stream`.  One launch; in
+ * a batch of one size the kernel counts the finished pixels of each of eight
+ * caller ranges, the calling thread polls the counts and copies a range back
+ * on a library-owned stream as soon as it is complete, while the kernel runs
+ * on (same pmfs bit for bit as the device-buffer call).
  */
 SPL_API spl_status_t spl_batch_stationary_host(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
                                        const float *h_warm, float *h_out, spl_report_t *h_reports,
@@ -341,9 +342,10 @@ SPL_API spl_status_t spl_batch_stationary_learned(spl_mlp_t *m, const spl_pixel_
                                                   spl_report_t *h_reports, void *stream,
                                                   const spl_batch_opts_t *opts /* nullable; warm fields ignored */);
 /* The same from and to host memory: pmfs into h_out (packed in caller order,
- * sum of n_bins floats; pinned memory copies fastest).  A batch of one size
- * runs as four consecutive ranges whose device-to-host copies overlap the next
- * range's compute (same pmfs bit for bit). */
+ * sum of n_bins floats; pinned memory copies fastest).  As
+ * spl_batch_stationary_host, each of eight caller ranges of a batch of one
+ * size is copied back as soon as the kernel has finished it (same pmfs bit
+ * for bit). */
 SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_pixel_t *h_pixels, int32_t n,
                                                        double tol, int32_t max_iter, float *h_out,
                                                        spl_report_t *h_reports, void *stream,

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cstdlib>
 #include <functional>
 #include <map>
@@ -739,10 +741,17 @@ struct BatchWorkspace {
     bool timed = false;
     // copies of the host-buffer entry points overlap the next range's compute
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_range = nullptr;
     // barrier words and set counters of the multi-chain launch
     unsigned *multi_words = nullptr;
     size_t multi_words_cap = 0;
+    // host-buffer calls: finished-pixel counts per caller range, their pinned
+    // mirror, the stream that polls them and the end-of-kernel event
+    int *range_done = nullptr;
+    size_t range_done_cap = 0;
+    int *h_range_done = nullptr;
+    size_t h_range_done_cap = 0;
+    cudaStream_t poll_stream = nullptr;
+    cudaEvent_t ev_end = nullptr;
 };
 
 constexpr int kMaxDevices = 64;
@@ -980,16 +989,14 @@ spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int n
 
 // Launches the persistent batch kernel; out/warm are packed by caller order.
 // tune: 0 measured configuration (cached), 1 the fixed heuristic, 2 the
-// caller's threads and state level.  chunks > 1 splits the work list into
-// that many consecutive ranges (each still filling the GPU), one launch each,
-// with after_range(start, count) called once a range is enqueued.
-using RangeFn = std::function<spl_status_t(int32_t, int32_t)>;
+// caller's threads, state level and columns per thread.  range_done (device,
+// [nranges], zeroed) receives the counts of finished pixels per caller range.
 spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int32_t max_iter, const float *d_warm,
                        int warm_kind, int warm_ld, int min_iter, int threads_req, float *d_out,
                        const int64_t *d_offsets,
                        cudaStream_t s, bool time_kernel = false, int structured = 0, int flux_kind = 0,
-                       int tune = 0, int level_req = -1, int chunks = 1, const RangeFn *after_range = nullptr,
-                       int cols_req = 0) {
+                       int tune = 0, int level_req = -1, int cols_req = 0, int *range_done = nullptr,
+                       int nranges = 0) {
     const int npad = batch_pad_len(nmax);
     const bool st_kind = structured == SPL_PASS_STRUCTURED;
     const int fault = injected_fault();
@@ -1055,13 +1062,12 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
         if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
         SPL_CU(cudaEventRecord(ws.ev0, s));
     }
-    const int per_wave = std::max(1, cfg.bps * num_sms_current());
-    const int K = std::max(1, std::min(chunks, n / (4 * per_wave)));
-    for (int c = 0; c < K; ++c) {
-        const int32_t lo = (int32_t)((int64_t)n * c / K), hi = (int32_t)((int64_t)n * (c + 1) / K);
-        if ((st = launch_cfg(ws, a, cfg, lo, hi - lo, npad, s)) != SPL_OK) return st;
-        if (after_range && (st = (*after_range)(lo, hi - lo)) != SPL_OK) return st;
+    if (range_done) {   // counted only in the launch that produces the result (not in tuning samples)
+        a.range_done = range_done;
+        a.nranges = nranges;
+        a.range_n = n;
     }
+    if ((st = launch_cfg(ws, a, cfg, 0, n, npad, s)) != SPL_OK) return st;
     if (time_kernel) {
         SPL_CU(cudaEventRecord(ws.ev1, s));
         ws.timed = true;
@@ -1124,7 +1130,7 @@ extern "C" spl_status_t spl_batch_stationary_ex(const spl_pixel_t *h_pixels, int
     const int cols = opts ? opts->cols : 0;
     if (cols != 0 && cols != 4 && cols != 8) return SPL_EINVAL;
     st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, kind, ld, min_iter, threads, d_out, d_offsets, s, timed,
-                   structured, flux_kind, tune, tune == 2 ? level : -1, 1, nullptr, cols);
+                   structured, flux_kind, tune, tune == 2 ? level : -1, cols);
     if (st != SPL_OK) return st;
     if (h_reports) return collect_reports(*ws, n, h_reports, s);
     // The pinned work list is read by the copy engine asynchronously; keep the
@@ -1140,9 +1146,10 @@ extern "C" spl_status_t spl_batch_stationary(const spl_pixel_t *h_pixels, int32_
 }
 
 // Host-buffer batch: pmfs into pinned or pageable h_out (packed in caller
-// order), reports into h_reports (may be NULL).  A batch of one size runs as
-// four consecutive ranges whose device-to-host copies (on a second stream)
-// overlap the next range's compute; other batches run as one launch.
+// order), reports into h_reports (may be NULL).  One launch; in a batch of
+// one size the copy-back of each of eight caller ranges (on a second stream)
+// starts as soon as the kernel has finished that range, overlapping the rest
+// of the kernel.
 spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double tol, int32_t max_iter,
                                  const float *d_warm, const float *h_warm, int warm_kind, int warm_ld, float *h_out,
                                  spl_report_t *h_reports, cudaStream_t s, const spl_batch_opts_t *opts) {
@@ -1182,27 +1189,66 @@ spl_status_t spl::batch_host_run(const spl_pixel_t *h_pixels, int32_t n, double 
         warm_ld = 0;
     }
     if (!ws->copy_stream) SPL_CU(cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking));
-    if (!ws->ev_range) SPL_CU(cudaEventCreateWithFlags(&ws->ev_range, cudaEventDisableTiming));
     float *d_out = ws->d_out;
     cudaStream_t cs = ws->copy_stream;
-    cudaEvent_t ev = ws->ev_range;
-    // in a batch of one size the work list keeps the caller's order, so a
-    // range of it is a contiguous slice of the packed output
-    const RangeFn copy_range = [&](int32_t lo, int32_t cnt) -> spl_status_t {
-        const int64_t o0 = uniform ? off[(size_t)lo] : 0, o1 = uniform ? off[(size_t)(lo + cnt)] : (int64_t)total;
-        if (!uniform && lo + cnt < n) return SPL_OK;      // one copy after the last range
-        SPL_CU(cudaEventRecord(ev, s));
-        SPL_CU(cudaStreamWaitEvent(cs, ev, 0));
+    if (!uniform) {
+        // ragged batch: the work list is sorted by size, so the output is
+        // copied in one piece after the launch
+        st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, warm_kind, warm_ld, min_iter, threads, d_out, nullptr, s,
+                       false, structured, flux_kind, tune, tune == 2 ? level : -1, opts ? opts->cols : 0);
+        if (st != SPL_OK) return st;
+        SPL_CU(cudaMemcpyAsync(h_out, d_out, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+        if (h_reports) return collect_reports(*ws, n, h_reports, s);
+        SPL_CU(cudaStreamSynchronize(s));
+        return SPL_OK;
+    }
+    // A batch of one size keeps the caller's order in the work list, so each
+    // of kHostRanges caller ranges is a contiguous slice of the output.  One
+    // launch runs the whole batch; the kernel counts each range's finished
+    // pixels, this thread polls the counts (a small copy on its own stream)
+    // and starts a range's copy-back as soon as its count is full, while the
+    // kernel runs on.  The wait ends when the kernel's end event completes.
+    constexpr int kHostRanges = 8;
+    const int K = std::min<int32_t>(kHostRanges, n);
+    if ((e = grow(&ws->range_done, &ws->range_done_cap, (size_t)K)) != cudaSuccess)
+        return status_of_alloc(e, "range counts");
+    if ((e = grow_host(&ws->h_range_done, &ws->h_range_done_cap, (size_t)K)) != cudaSuccess)
+        return status_of_alloc(e, "pinned range counts");
+    if (!ws->poll_stream) SPL_CU(cudaStreamCreateWithFlags(&ws->poll_stream, cudaStreamNonBlocking));
+    if (!ws->ev_end) SPL_CU(cudaEventCreateWithFlags(&ws->ev_end, cudaEventDisableTiming));
+    SPL_CU(cudaMemsetAsync(ws->range_done, 0, sizeof(int) * K, s));
+    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, warm_kind, warm_ld, min_iter, threads, d_out, nullptr, s,
+                   false, structured, flux_kind, tune, tune == 2 ? level : -1, opts ? opts->cols : 0,
+                   ws->range_done, K);
+    if (st != SPL_OK) return st;
+    SPL_CU(cudaEventRecord(ws->ev_end, s));
+    bool sent[kHostRanges] = {};
+    int nsent = 0;
+    auto send = [&](int c) -> spl_status_t {
+        const int64_t lo = (int64_t)n * c / K, hi = (int64_t)n * (c + 1) / K;
+        const int64_t o0 = off[(size_t)lo], o1 = off[(size_t)hi];
         SPL_CU(cudaMemcpyAsync(h_out + o0, d_out + o0, sizeof(float) * (size_t)(o1 - o0), cudaMemcpyDeviceToHost,
                                cs));
+        sent[c] = true;
+        ++nsent;
         return SPL_OK;
     };
-    st = run_batch(*ws, n, nmax, tol, max_iter, d_warm, warm_kind, warm_ld, min_iter, threads, d_out, nullptr, s,
-                   false, structured, flux_kind, tune, tune == 2 ? level : -1, uniform ? 4 : 1, &copy_range,
-                   opts ? opts->cols : 0);
-    if (st != SPL_OK) {
-        cudaStreamSynchronize(cs);
-        return st;
+    while (nsent < K) {
+        const cudaError_t q = cudaEventQuery(ws->ev_end);
+        if (q == cudaSuccess) {            // the kernel is done: copy whatever is left
+            for (int c = 0; c < K; ++c)
+                if (!sent[c] && (st = send(c)) != SPL_OK) return st;
+            break;
+        }
+        if (q != cudaErrorNotReady) return cuda_fail(q, "batch kernel");
+        SPL_CU(cudaMemcpyAsync(ws->h_range_done, ws->range_done, sizeof(int) * K, cudaMemcpyDeviceToHost,
+                               ws->poll_stream));
+        SPL_CU(cudaStreamSynchronize(ws->poll_stream));
+        for (int c = 0; c < K; ++c) {
+            const int64_t size = (int64_t)n * (c + 1) / K - (int64_t)n * c / K;
+            if (!sent[c] && ws->h_range_done[c] >= size && (st = send(c)) != SPL_OK) return st;
+        }
+        if (nsent < K) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     SPL_CU(cudaStreamSynchronize(cs));
     if (h_reports) return collect_reports(*ws, n, h_reports, s);

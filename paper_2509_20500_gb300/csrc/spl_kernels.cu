@@ -722,6 +722,13 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
             a.reports[p.index] = r;
         }
         __syncthreads();
+        // host-buffer calls: the pixel's range gains one finished pixel, after
+        // every thread's output write (the host copies a range once its count
+        // is full)
+        if (a.range_done != nullptr && tid == 0) {
+            __threadfence();
+            atomicAdd(a.range_done + (int)(((long long)(p.index + 1) * a.nranges - 1) / a.range_n), 1);
+        }
     }
 }
 

@@ -49,6 +49,9 @@ struct BatchArgs {
     int structured;          // 1: O(N) scan form of the power step (same result, no N^2 pass)
     int row_scan;            // 1 (dense steps): row sums by the scans of the structured form, not a dense pass
     int cols;                // columns per thread of the dense passes: 4, or 8 (any other value)
+    int *range_done;         // NULL, or [nranges] counts of finished pixels per caller range (host-buffer calls)
+    int nranges;             // caller ranges [range_n c / nranges, range_n (c+1) / nranges)
+    int range_n;             // pixels of the call
     int flux_kind;           // spl_flux_kind_t: 0 point flux (Sec. 3.4), 1 bin-integrated
     PixelConst *pconst;      // [n] per-pixel constants (work-list order), written by launch_batch
 };

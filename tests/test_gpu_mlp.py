@@ -225,16 +225,16 @@ def test_checkpoint_resumes_training_exactly(spl, tmp_path):
 
 
 def test_learned_host_entry_point_matches_device_path(spl):
-    """spl_batch_stationary_learned_host (four ranges with overlapped copies
-    for a batch of one size) gives the device path's pmfs and reports bit for
-    bit, into pinned host memory."""
+    """spl_batch_stationary_learned_host (eight ranges copied back while the
+    kernel runs, for a batch of one size) gives the device path's pmfs and
+    reports bit for bit, into pinned host memory."""
     train = W.training(4096, seed=2)
     tgt, _, _ = spl.batch_stationary(train, tol=1e-6)
     tgt = tgt.view(len(train), 2000)
     net = spl.MLP(max_batch=8192, seed=1)
     for b in range(4):
         net.train_step(spl.pixels_to_c(train[b * 1024:(b + 1) * 1024]), 1024, tgt[b * 1024:(b + 1) * 1024], lr=2e-3)
-    px = W.array_pixels(8192, seed=79)           # at least 16 x SMs pixels: four ranges
+    px = W.array_pixels(8192, seed=79)           # eight ranges of 1024 pixels
     pk = spl.SPL_PASS_DENSE_ROWSCAN              # the timed path's pass kind
     d, off, rd = net.batch_stationary(px, tol=1e-6, pass_kind=pk)
     h, off2, rh = net.batch_stationary_host(px, tol=1e-6, pass_kind=pk)

@@ -574,9 +574,9 @@ def test_batch_host_entry_point(spl):
 
 @pytest.mark.parametrize("kind", ["one size", "ragged"])
 def test_batch_host_entry_point_ranges(spl, kind):
-    """A batch of one size large enough for four ranges (copies overlapped
-    with compute) and a ragged one (one launch): the host entry point gives
-    the device path's pmfs and reports bit for bit."""
+    """A batch of one size (eight ranges, each copied back while the kernel
+    runs on) and a ragged one (one copy after the launch): the host entry
+    point gives the device path's pmfs and reports bit for bit."""
     if kind == "one size":
         px = W.array_pixels(6000, seed=16, n_bins=700)
     else:
