@@ -37,8 +37,11 @@ def test_stored_traffic_matches_the_committed_kernel():
         t = b.stored_traffic(arm)
         a = d["arms"][arm]
         assert t == a["dram_bytes_read_per_launch"] + a["dram_bytes_write_per_launch"]
-        # no re-reads: within 3 % of the algorithmic bytes of a launch
-        assert abs(t / a["algorithmic_bytes_per_launch"] - 1.0) < 0.03
+        # no re-reads: at most 3 % above the algorithmic bytes of a launch; below
+        # them by at most what the 129 MB L2 still holds (written, not yet
+        # evicted) when the kernel ends
+        alg = a["algorithmic_bytes_per_launch"]
+        assert alg - 129e6 <= t <= 1.03 * alg
 
 
 def test_comment_edits_keep_the_key_and_code_edits_drop_it(tmp_path):
