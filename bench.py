@@ -786,7 +786,8 @@ def run_profile_case(name: str) -> int:
     line): each case launches its kernel twice on the same inputs, so a
     capture with `-k regex:<kernel> -s 1 -c 1` takes a warm, full-size launch.
       batch_dense / batch_structured: 4096 pixels of the array workload (N = 2000),
-          fixed launch heuristic (no tuning launches), dense or O(N) step;
+          fixed launch heuristic (no tuning launches), the timed path's dense steps
+          (row sums from scans) or the O(N) step;
       gemv / build / chain_run: one N = 10000 pixel (t_d = 75, S = 0.5), the
           materialised power step, the materialised build, the fused chain;
       chain_multi: the 12 pixels of the N = 10000 dead-time and signal sweep
@@ -799,7 +800,7 @@ def run_profile_case(name: str) -> int:
     torch.cuda.set_device(0)
     if name in ("batch_dense", "batch_structured"):
         px = W.array256()[:4096]
-        pk = spl.SPL_PASS_DENSE if name == "batch_dense" else spl.SPL_PASS_STRUCTURED
+        pk = spl.SPL_PASS_DENSE_ROWSCAN if name == "batch_dense" else spl.SPL_PASS_STRUCTURED
         for _ in range(2):
             _, _, r = spl.batch_stationary(px, tol=TOL, max_iter=MAX_ITER, pass_kind=pk, tune=1)
             assert np.all(r["status"] == 0)
