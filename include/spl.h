@@ -359,7 +359,7 @@ SPL_API spl_status_t spl_batch_stationary_learned_host(spl_mlp_t *m, const spl_p
  *   (the call runs on that stream).  One cooperative launch (at most 32
  *   chains per launch; more run as consecutive launches) runs the chains in
  *   lockstep: at every power step the work of the chains still iterating
- *   (128-column tile x 32-row units, chain after chain) is split evenly over
+ *   (256-column tile x 32-row units, chain after chain) is split evenly over
  *   all resident CTAs, then their bins likewise for the normalisation, with
  *   one grid barrier per step.  Each chain has its own stop rule; a chain that
  *   stops leaves the step's work to the others, so no CTA idles while any
@@ -393,7 +393,7 @@ SPL_API spl_status_t spl_chains_plan(const int32_t *n_bins, int32_t n, int32_t s
 /* Plan of a fused chain's persistent iteration (host arithmetic only, no GPU
  * needed): on a GPU with `sms` SMs keeping `blocks_per_sm` CTAs resident, a
  * chain of n_bins bins runs on `grid` CTAs; its column pass is cut into
- * tiles x row_blocks equal units (128 columns x 32 rows, vlen = rows padded),
+ * tiles x row_blocks equal units (256 columns x 32 rows, vlen = rows padded),
  * CTA b taking units [b U / grid, (b+1) U / grid) with U = tiles x
  * row_blocks; `segs` partial slots per CTA; at most `chunk` rows staged in
  * shared memory at once.  SPL_EINVAL on bad arguments. */

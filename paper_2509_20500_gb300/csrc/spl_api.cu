@@ -235,7 +235,7 @@ static void run_partition(long long U, int RB, int G, int *segs, long long *umax
 }
 
 // Plan of the persistent fused iteration (host arithmetic only): as many CTAs
-// as stay resident (at most one per work unit), the work units (128-column
+// as stay resident (at most one per work unit), the work units (256-column
 // tile x 32-row block) split evenly over them, the partial slots one CTA
 // needs and the rows it stages at once.
 extern "C" spl_status_t spl_chain_run_plan(int32_t n_bins, int32_t sms, int32_t blocks_per_sm, spl_run_plan_t *out) {
@@ -273,7 +273,7 @@ static spl_status_t plan_run(spl_chain *c) {
     SPL_CU(dalloc(&c->run_vb, 2 * (size_t)c->vlen));
     SPL_CU(cudaMemset(c->run_vb, 0, 2 * sizeof(float) * c->vlen));
     SPL_CU(dalloc(&c->run_pi, (size_t)c->N));
-    SPL_CU(dalloc(&c->run_tsum, 8 * (size_t)T));   // [2][T][4] warp partials of the tile sums
+    SPL_CU(dalloc(&c->run_tsum, 2 * (size_t)(chain_run_tile_cols() / 32) * T));   // [2][T][warps] tile-sum partials
     c->run_part_cap = (size_t)G * pl.segs * chain_run_tile_cols();
     SPL_CU(dalloc(&c->run_part, c->run_part_cap));
     c->run_blk_cap = 2 * (size_t)G * 4;
@@ -1335,11 +1335,11 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
             coff[g] = off;
             off += chains[k0 + g]->N;
         }
-        long long U = 0;
+        long long Us[2] = {0, 0};   // units of each set's first step
         for (int q = 0; q < m; ++q) {
             const int g = order[q];
             spl_chain *c = chains[k0 + g];
-            U += (long long)c->run_T * c->run_RB;
+            Us[q < n0 ? 0 : 1] += (long long)c->run_T * c->run_RB;
             const int slots = chain_multi_slots(c->N, grid);
             const size_t need_part = (size_t)c->run_T * slots * chain_run_tile_cols();
             const size_t need_blk = 2 * (size_t)grid * 4;
@@ -1367,9 +1367,13 @@ extern "C" spl_status_t spl_chains_stationary(spl_chain_t *const *chains, int32_
             M.off[q] = coff[g];
             M.idx[q] = g;
         }
-        // rows of one staging buffer: a window is at most chain_run_max_chunk()
-        // rows and at most one CTA's share of the first step's units
-        const long long per_cta = (U + std::min<long long>(grid, U) - 1) / std::min<long long>(grid, U);
+        // rows of one staging buffer (the kernel's windows never exceed it): at
+        // most chain_run_max_chunk(), and no more than the largest share of a
+        // CTA in the first step of its set (grid / nsets CTAs per set)
+        long long per_cta = 1;
+        const long long Gs = grid / M.nsets;
+        for (int q = 0; q < M.nsets; ++q)
+            if (Us[q] > 0) per_cta = std::max(per_cta, (Us[q] + std::min(Gs, Us[q]) - 1) / std::min(Gs, Us[q]));
         M.chunk = (int)std::min<long long>(chain_run_max_chunk(), 32 * per_cta);
         SPL_CU(launch_chain_multi(M, grid, d_out, ws->reps + k0, s));
     }

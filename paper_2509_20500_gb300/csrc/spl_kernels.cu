@@ -1227,7 +1227,7 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
 //
 // One cooperative launch (all CTAs resident) runs the steps of one chain
 // with one grid barrier per step.  The column pass is cut into equal work
-// units, (column tile of 128 columns) x (block of 32 rows), in tile-major
+// units, (column tile of 256 columns) x (block of 32 rows), in tile-major
 // order; CTA b takes the contiguous units [b U / G, (b+1) U / G), which cover
 // at most a few tiles.  Per step k:
 //   pass        for each tile segment of its units, the CTA stages the rows
@@ -1252,8 +1252,9 @@ __global__ void __launch_bounds__(NT) tri_split_kernel(TriSplitArgs a) {
 
 constexpr int kRunNT = 256;
 constexpr int kRunW = kRunNT / 32;
-constexpr int kRunC = 4;
+constexpr int kRunC = 8;
 constexpr int kRunTW = 32 * kRunC;                      // columns per tile (one warp span)
+constexpr int kRunTP = kRunTW / 32;                     // warp partials of a tile's sum
 constexpr int kRunMaxChunk = 8192;                      // rows of v in shared memory at once
 constexpr int kBarGen = 32;                             // a barrier's slot is 2 kBarGen words (its own lines)
 static_assert(3 * 2 * kBarGen <= kMultiCountWord, "three barriers before the set counters");
@@ -1346,7 +1347,7 @@ __device__ __forceinline__ int run_owner(long long u, long long U, int G) {
 // run_tile_reduce); a shared tile leaves the CTA's partial in its slot.
 // The pass ran on the unnormalised broadcast vector of the previous step; inv
 // (1 / sum of its y) normalises the column sums here.  The tile sum is left
-// as four warp partials, tdst[4 t + w].
+// as kRunTP warp partials, tdst[kRunTP t + w].
 __device__ __forceinline__ void run_flush(const ChainRunArgs &a, int t, int t_first, int b, bool own_first,
                                           bool own_last, int t_last, const float (&acc)[kRunC],
                                           float (*wred)[kRunTW], float inv, float *ydst, float *vdst,
@@ -1374,7 +1375,7 @@ __device__ __forceinline__ void run_flush(const ChainRunArgs &a, int t, int t_fi
                 p = 0.f;
             }
             const float ts = warp_sum(p);
-            if (lane == 0) tdst[4 * t + wid] = ts;
+            if (lane == 0) tdst[kRunTP * t + wid] = ts;
         }
     }
     __syncthreads();   // wred is reused
@@ -1402,7 +1403,7 @@ __device__ __forceinline__ void run_tile_reduce(const ChainRunArgs &a, int t, lo
     }
     if (tid < kRunTW) {
         const float ts = warp_sum(yv);
-        if ((tid & 31) == 0) tdst[4 * t + (tid >> 5)] = ts;
+        if ((tid & 31) == 0) tdst[kRunTP * t + (tid >> 5)] = ts;
     }
 }
 
@@ -1435,8 +1436,9 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
     const float *vsrc = a.v0;               // h^(0) = pi^(0)_{(k-l) mod N} rho_k
     float inv = 1.f;
     // windows of this CTA's units, staged as 16-byte async copies into buffer
-    // w & 1 (a.chunk rows each); unit u holds rows (u mod RB) 32 ... + 31
-    constexpr int kWinUnits = kRunMaxChunk / 32;
+    // w & 1 (a.chunk rows each, so a window is at most a.chunk / 32 units);
+    // unit u holds rows (u mod RB) 32 ... + 31
+    const int kWinUnits = a.chunk / 32;
     const int nwin = (int)((u1 - u0 + kWinUnits - 1) / kWinUnits);
     auto stage = [&](int w) {
         const long long wu0 = u0 + (long long)w * kWinUnits, wu1 = min(u1, wu0 + kWinUnits);
@@ -1457,7 +1459,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
     for (int k = 1;; ++k) {
         float *ydst = a.y + (k & 1) * vlen;
         float *vdst = a.vb + (k & 1) * vlen;
-        float *tdst = a.tsum + (size_t)(k & 1) * 4 * T;
+        float *tdst = a.tsum + (size_t)(k & 1) * kRunTP * T;
         // ---- pass k, in windows of at most kRunMaxChunk rows staged in unit order
         // into two shared buffers: window w + 1 is in flight while w is summed
         // (window 0 was issued before the previous step's normalisation)
@@ -1559,7 +1561,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
             red5[2] = x0.z + x1.z;
             red5[3] = x0.w + x1.w;
         }
-        for (int t = tid; t < 4 * T; t += kRunNT) red5[4] += __ldcg(tdst + t);
+        for (int t = tid; t < kRunTP * T; t += kRunNT) red5[4] += __ldcg(tdst + t);
         const int jf = j0 + tid;
         float fy = 0.f, fp = 0.f, f1 = 0.f, f2 = 0.f;
         if (jf < j1) {
@@ -1622,7 +1624,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
 
 // Several chains in lockstep in one cooperative launch.  Step k of every
 // chain still iterating runs in the same pass: the units of the active chains
-// (the chain's 128-column tiles x 32-row blocks, chain after chain) are split
+// (the chain's 256-column tiles x 32-row blocks, chain after chain) are split
 // evenly over the CTAs, each CTA leaves one partial per tile it touches and
 // the last CTA to finish a shared tile adds them in CTA order; after one grid
 // barrier the active chains' bins, chain after chain, are split evenly over
@@ -1637,7 +1639,7 @@ __device__ __forceinline__ long long lk_owner(long long u, long long U, int G) {
 
 // Flush of tile t of chain g at the end of this CTA's segment of it: the warp
 // partials added in warp order and normalised by inv; a tile that only this
-// CTA touches is finished (y, v, the tile sum as four warp partials), a shared
+// CTA touches is finished (y, v, the tile sum as one partial per warp), a shared
 // tile leaves this CTA's partial in slot b - bf.
 __device__ __forceinline__ void lk_flush(const ChainRunArgs &c, int t, int k, bool owned, int slot,
                                          const float (&acc)[kRunC], float (*wred)[kRunTW], float inv) {
@@ -1663,7 +1665,7 @@ __device__ __forceinline__ void lk_flush(const ChainRunArgs &c, int t, int k, bo
                 p = 0.f;
             }
             const float ts = warp_sum(p);
-            if (lane == 0) c.tsum[(size_t)(k & 1) * 4 * c.T + 4 * t + wid] = ts;
+            if (lane == 0) c.tsum[(size_t)(k & 1) * kRunTP * c.T + kRunTP * t + wid] = ts;
         }
     }
     __syncthreads();   // wred is reused
@@ -1686,7 +1688,7 @@ __device__ __forceinline__ void lk_tile_reduce(const ChainRunArgs &c, int t, int
     }
     if (tid < kRunTW) {
         const float ts = warp_sum(yv);
-        if ((tid & 31) == 0) c.tsum[(size_t)(k & 1) * 4 * c.T + 4 * t + (tid >> 5)] = ts;
+        if ((tid & 31) == 0) c.tsum[(size_t)(k & 1) * kRunTP * c.T + kRunTP * t + (tid >> 5)] = ts;
     }
 }
 
@@ -1704,7 +1706,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     __shared__ StopState s_st[kChainMultiMax];
     __shared__ int s_fin[kChainMultiMax];
     __shared__ int s_tile[6];                           // shared first / last tile: chain, tile, slots
-    constexpr int kWinUnits = kRunMaxChunk / 32;
+    const int kWinUnits = m.chunk / 32;   // a staging buffer holds m.chunk rows
     __shared__ int s_reg[2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned gen = 0u;
@@ -1944,8 +1946,8 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         for (int q = wid; q < n; q += kRunW) {
             if (!(mask >> q & 1u)) continue;
             const ChainRunArgs &c = cc[q];
-            const float *ts = c.tsum + (size_t)(k & 1) * 4 * c.T;
-            const int nts = 4 * c.T;
+            const float *ts = c.tsum + (size_t)(k & 1) * kRunTP * c.T;
+            const int nts = kRunTP * c.T;
             float sy = 0.f;
             for (int i = lane; i < nts; i += 128) {   // four independent loads per lane in flight
                 const float x0 = __ldcg(ts + i);

@@ -97,7 +97,7 @@ struct ChainRunArgs {
     float *d1, *d2;          // [N] the last two steps
     float *y;                // [2][vlen] unnormalised iterates (alternating)
     float *vb;               // [2][vlen] next broadcast vectors (alternating), zero past N
-    float *tsum;             // [2][T][4] tile sums of y, as four warp partials per tile
+    float *tsum;             // [2][T][TW / 32] tile sums of y, one partial per warp of a tile
     float *part;             // [grid][segs][tile columns] per-CTA partial column sums
     float *blk;              // [2][grid][4] per-CTA step statistics (16-byte aligned)
     int *tile_ticket;        // [T] arrival counters, zero between uses

@@ -1,5 +1,5 @@
 """Work partition of the fused chain's persistent iteration (host arithmetic,
-no GPU): every (128-column tile, 32-row block) unit has exactly one CTA, the
+no GPU): every (256-column tile, 32-row block) unit has exactly one CTA, the
 owner formula the kernel uses finds it, a CTA shares at most its first and
 last tile with other CTAs, its partial slots fit `segs`, and the rows it
 stages at once fit `chunk`."""
@@ -7,6 +7,8 @@ import numpy as np
 import pytest
 
 from paper_2509_20500_gb300 import spl
+
+TW = 256   # columns of a tile: one warp span of the fused chain kernels, 8 columns per lane
 
 
 def _owner(u, U, G):
@@ -18,7 +20,7 @@ def _check(n, sms, bps):
     pl = spl.chain_run_plan(n, sms, bps)
     G, T, RB, segs, chunk, vlen = (pl[k] for k in ("grid", "tiles", "row_blocks", "segs", "chunk", "vlen"))
     assert vlen >= n and vlen % 128 == 0 and RB == vlen // 32
-    assert T == (n + 127) // 128
+    assert T == (n + TW - 1) // TW
     U = T * RB
     assert 1 <= G <= min(bps * sms, 512, U)
     start = [b * U // G for b in range(G + 1)]
@@ -57,11 +59,12 @@ def test_partition_invariants(n):
 
 
 def test_partition_sizes_used_by_the_gpu_tests():
-    # N = 10000: two tiles per CTA at most; N = 18000: more rows than one window
+    # N = 10000: two tiles per CTA at most; N = 26000: more rows than one
+    # window (274 units of 32 rows > 256)
     p = _check(10000, 152, 2)
-    assert (p["grid"], p["tiles"], p["segs"], p["chunk"]) == (304, 79, 2, 2656)
-    p = _check(18000, 152, 2)
-    assert p["chunk"] == 8192 and p["segs"] == 2
+    assert (p["grid"], p["tiles"], p["segs"], p["chunk"]) == (304, 40, 2, 1344)
+    p = _check(26000, 152, 2)
+    assert p["chunk"] == 8192 and p["segs"] == 2 and p["tiles"] * p["row_blocks"] > 256 * p["grid"]
 
 
 def test_plan_rejects_bad_arguments():
@@ -76,7 +79,7 @@ def _tile_contributors(n_bins, active, G):
     """Largest number of CTAs one column tile of each active chain meets when
     the units of the active chains, chain after chain, are split as
     [b U / G', (b+1) U / G') over G' = min(G, U) CTAs (the kernel's partition)."""
-    T = [(n + 127) // 128 for n in n_bins]
+    T = [(n + TW - 1) // TW for n in n_bins]
     RB = [spl.chain_run_plan(n, 1, 1)["vlen"] // 32 for n in n_bins]
     U = sum(T[g] * RB[g] for g in active)
     Ge = min(G, U)
