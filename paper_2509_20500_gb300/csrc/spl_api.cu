@@ -833,14 +833,10 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 //
 // A configuration is the block size (256 or 512 threads), the state level
 // (how many per-pixel vectors live in shared memory) and the blocks per SM.
-// The state level and the blocks per SM only move vectors between shared and
-// global memory and change how many pixels run at once, never the order of a
-// sum, so they give the same pmfs bit for bit; the block size changes the
-// block reductions' order (rounding) and is not measured, only taken when
-// the caller asks for it.  The rest is measured: on the first large batch of
-// a kind (padded N, pass kind, SM count) every feasible 256-thread
-// configuration runs a sample of the work list (after an untimed launch that
-// absorbs module loading), the fastest per pixel is kept in a cache, and
+// Launch configuration of the batch kernel: block size, columns per thread,
+// state level and blocks per SM.  On the first large batch of a kind (padded
+// N, pass kind, SM count) the feasible configurations are timed on a sample
+// of the work list (tune_batch), the pick is kept in a cache, and
 // SPL_TUNE_CACHE (a file path, optional) keeps the cache across processes.
 
 struct LaunchCfg {
@@ -947,19 +943,28 @@ spl_status_t launch_cfg(BatchWorkspace &ws, BatchArgs a, const LaunchCfg &cfg, i
 }
 
 // Times every feasible configuration on a sample of the work list and keeps
-// the fastest (per pixel).  State level and blocks per SM leave the pmfs
-// unchanged bit for bit; the block size (the order of the block reductions)
-// and the columns per thread (where the diagonal span cuts each column's sum
-// into chunks) change them within rounding.
+// the fastest.  State level and blocks per SM leave the pmfs unchanged bit
+// for bit; the block size (the order of the block reductions) and the columns
+// per thread (where the diagonal span cuts each column's sum into chunks)
+// change them within rounding.  The configurations differ by a few percent at
+// most, so the measurement guards against noise: a sample of up to
+// kTuneSamplePerSm pixels per SM (a short sample is dominated by the tail of
+// its last pixels), every configuration timed twice in two interleaved rounds
+// (the minimum counts), and the heuristic's configuration `heur` kept unless
+// another one beats it by more than kTuneMargin.
+constexpr int32_t kTuneSamplePerSm = 48;
+constexpr float kTuneMargin = 0.005f;
+
 spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int npad, bool structured,
-                        cudaStream_t s, LaunchCfg *best) {
+                        const LaunchCfg &heur, cudaStream_t s, LaunchCfg *best) {
     const int sms = num_sms_current();
-    const int32_t sample = std::min<int32_t>(n, 12 * sms);
+    const int32_t sample = std::min<int32_t>(n, kTuneSamplePerSm * sms);
     if (!ws.ev0) SPL_CU(cudaEventCreate(&ws.ev0));
     if (!ws.ev1) SPL_CU(cudaEventCreate(&ws.ev1));
-    float best_ms = INFINITY;
-    // block size and columns per thread (dense passes only), state level, and
-    // blocks per SM at the occupancy limit or one below
+    // the heuristic first, then block size and columns per thread (dense
+    // passes only), state level, and blocks per SM at the occupancy limit or
+    // one below
+    std::vector<LaunchCfg> cand{heur};
     const int nthr = structured ? 1 : 2, ncol = structured ? 1 : 2;
     for (int ti = 0; ti < nthr; ++ti)
     for (int ci = 0; ci < ncol; ++ci)
@@ -969,22 +974,37 @@ spl_status_t tune_batch(BatchWorkspace &ws, const BatchArgs &a, int32_t n, int n
         for (int bps = top.bps; bps >= std::max(1, top.bps - 1); --bps) {
             LaunchCfg cfg = top;
             cfg.bps = bps;
-            // untimed: loads the kernel's module and settles the clocks
-            spl_status_t st = launch_cfg(ws, a, cfg, 0, std::min<int32_t>(sample, cfg.bps * sms), npad, s);
-            if (st != SPL_OK) return st;
+            if (cfg.threads == heur.threads && cfg.level == heur.level && cfg.bps == heur.bps &&
+                cfg.cols == heur.cols)
+                continue;
+            cand.push_back(cfg);
+        }
+    }
+    std::vector<float> ms(cand.size(), INFINITY);
+    for (int round = 0; round < 2; ++round) {
+        for (size_t i = 0; i < cand.size(); ++i) {
+            const LaunchCfg &cfg = cand[i];
+            spl_status_t st;
+            if (round == 0) {
+                // untimed: loads the kernel's module and settles the clocks
+                st = launch_cfg(ws, a, cfg, 0, std::min<int32_t>(sample, cfg.bps * sms), npad, s);
+                if (st != SPL_OK) return st;
+            }
             SPL_CU(cudaEventRecord(ws.ev0, s));
             if ((st = launch_cfg(ws, a, cfg, 0, sample, npad, s)) != SPL_OK) return st;
             SPL_CU(cudaEventRecord(ws.ev1, s));
             SPL_CU(cudaEventSynchronize(ws.ev1));
-            float ms = 0.f;
-            SPL_CU(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                *best = cfg;
-            }
+            float t = 0.f;
+            SPL_CU(cudaEventElapsedTime(&t, ws.ev0, ws.ev1));
+            ms[i] = std::min(ms[i], t);
         }
     }
-    return std::isfinite(best_ms) ? SPL_OK : SPL_EINVAL;
+    size_t bi = 0;
+    for (size_t i = 1; i < cand.size(); ++i)
+        if (ms[i] < ms[bi]) bi = i;
+    if (!(ms[0] <= ms[bi] * (1.f + kTuneMargin))) *best = cand[bi];
+    else *best = cand[0];
+    return std::isfinite(ms[bi]) ? SPL_OK : SPL_EINVAL;
 }
 
 // Launches the persistent batch kernel; out/warm are packed by caller order.
@@ -1048,7 +1068,7 @@ spl_status_t run_batch(BatchWorkspace &ws, int32_t n, int nmax, double tol, int3
                 c2.bps = v[2];
                 cfg = c2;
             } else if (n >= kTuneMinPixels) {
-                if ((st = tune_batch(ws, a, n, npad, st_kind, s, &c2)) != SPL_OK) return st;
+                if ((st = tune_batch(ws, a, n, npad, st_kind, cfg, s, &c2)) != SPL_OK) return st;
                 cfg = c2;
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 tune_load_locked();

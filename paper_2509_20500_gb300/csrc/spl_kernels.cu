@@ -327,6 +327,52 @@ __device__ float block_scan(const float *v, float *out, int n, bool rev, float *
     return carry;
 }
 
+// rho_k = 1 / (S_k + eL P_k) for k < n <= 8 NT, from one pass over w: S_k =
+// sum_{j >= k} w_j (inclusive suffix) and P_k = sum_{j < k} w_j (exclusive
+// prefix), both accumulated outward from their own end (no subtraction from
+// the total, which would cancel where the suffix is small).  Thread t holds
+// w[8t .. 8t+8); the two thread-level scans run as warp shuffles in opposite
+// directions and the warp totals cross one barrier.  red needs 2 NT/32 floats.
+template <int NT>
+__device__ __forceinline__ void row_rho_scan(const float *w, float *rho, int n, float eL, float *red) {
+    constexpr int IT = 8, NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int e0 = tid * IT;
+    float x[IT], pe[IT], si[IT];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) x[i] = (e0 + i < n) ? w[e0 + i] : 0.f;
+    pe[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i < IT; ++i) pe[i] = pe[i - 1] + x[i - 1];
+    si[IT - 1] = x[IT - 1];
+#pragma unroll
+    for (int i = IT - 2; i >= 0; --i) si[i] = si[i + 1] + x[i];
+    float a = pe[IT - 1] + x[IT - 1], b = si[0];   // the thread's total, summed from each end
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ya = __shfl_up_sync(0xffffffffu, a, o);
+        const float yb = __shfl_down_sync(0xffffffffu, b, o);
+        if (lane >= o) a += ya;
+        if (lane + o < 32) b += yb;
+    }
+    float ax = __shfl_up_sync(0xffffffffu, a, 1);     // exclusive: lanes before this one
+    float bx = __shfl_down_sync(0xffffffffu, b, 1);   // exclusive: lanes after this one
+    if (lane == 0) ax = 0.f;
+    if (lane == 31) bx = 0.f;
+    if (lane == 31) red[wid] = a;
+    if (lane == 0) red[NW + wid] = b;
+    __syncthreads();
+    float wa = 0.f, wb = 0.f;
+    for (int q = 0; q < wid; ++q) wa += red[q];
+    for (int q = NW - 1; q > wid; --q) wb += red[NW + q];
+    const float offa = wa + ax, offb = wb + bx;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int k = e0 + i;
+        if (k < n) rho[k] = 1.f / ((si[i] + offb) + eL * (pe[i] + offa));
+    }
+}
+
 // ======================================================================
 // K5: persistent batch driver with the per-CTA matrix-free step
 // ======================================================================
@@ -509,10 +555,13 @@ __global__ void __launch_bounds__(NT, STRUCT ? kStructMinBlocks : (NT <= 256 ? S
         __syncthreads();
 
         // ---- row sums r'_k, rho_k = u_k / r'_k
-        if (STRUCT || a.row_scan) {
-            // r'_k / u_k = sum_{j >= k} w_j + eL sum_{j < k} w_j: an inclusive
-            // suffix scan and an inclusive prefix scan of w (prefix - w_k is the
-            // exclusive prefix, whose rounding is damped by eL).
+        if ((STRUCT || a.row_scan) && N <= 8 * NT) {
+            // r'_k / u_k = sum_{j >= k} w_j + eL sum_{j < k} w_j in one pass
+            row_rho_scan<NT>(gw, srho, N, eL, red);
+        } else if (STRUCT || a.row_scan) {
+            // the same from an inclusive suffix scan and an inclusive prefix
+            // scan of w over several tiles (prefix - w_k is the exclusive
+            // prefix, whose rounding is damped by eL)
             block_scan<NT>(gw, gy, N, false, red);      // gy = prefix
             block_scan<NT>(gw, sv, N, true, red);       // sv = suffix
             for (int k = tid; k < N; k += NT) srho[k] = 1.f / (sv[k] + eL * (gy[k] - gw[k]));

@@ -658,8 +658,10 @@ def test_structured_step_array_sample_vs_oracle(spl, kind):
 
 def test_structured_and_dense_steps_agree_on_ragged_batch(spl):
     """Both forms of the step, and the dense step with scan row sums, reach
-    the same pmf (each within 1e-6 L1 of the oracle) on uneven sizes,
-    including N above one scan tile (2048)."""
+    the same pmf on uneven sizes, including N above one scan tile (2048):
+    each within 1e-6 L1 of the oracle where the oracle runs (N <= 2000), and
+    within 2e-6 of each other everywhere (two results that each meet the
+    tolerance can be that far apart)."""
     a = W.random_small(30, seed=18, n_min=2, n_max=400)
     b = W.uneven(16, seed=19)
     b = b[b["n_bins"] <= 8000]
@@ -670,10 +672,11 @@ def test_structured_and_dense_steps_agree_on_ragged_batch(spl):
     assert np.all(rs["status"] == 0) and np.all(rr["status"] == 0)
     d, s, r = d.cpu().numpy(), s.cpu().numpy(), r.cpu().numpy()
     for k, p in enumerate(W.as_dicts(px)):
-        assert _l1(d[off[k]:off[k + 1]], s[off[k]:off[k + 1]]) < L1_TOL, (k, p["n_bins"])
-        assert _l1(d[off[k]:off[k + 1]], r[off[k]:off[k + 1]]) < L1_TOL, (k, p["n_bins"])
+        assert _l1(d[off[k]:off[k + 1]], s[off[k]:off[k + 1]]) < 2 * L1_TOL, (k, p["n_bins"])
+        assert _l1(d[off[k]:off[k + 1]], r[off[k]:off[k + 1]]) < 2 * L1_TOL, (k, p["n_bins"])
         if p["n_bins"] <= 2000:
             ref = oracle.stationary(p, shift=oracle.shift_l(p))
+            _assert_pmf(d[off[k]:off[k + 1]], ref, (k, p, "dense"))
             _assert_pmf(s[off[k]:off[k + 1]], ref, (k, p))
             _assert_pmf(r[off[k]:off[k + 1]], ref, (k, p, "rowscan"))
 
