@@ -65,6 +65,12 @@ namespace spl {
 #define SPL_TRI_UNROLL 4
 #endif
 constexpr int kTriUnroll = SPL_TRI_UNROLL;
+// The same for the single- and multi-chain kernels, whose pass pieces are
+// inlined one after the other (kOneCopy false) with 64-row chunks.
+#ifndef SPL_TRI_UNROLL_CHAIN
+#define SPL_TRI_UNROLL_CHAIN 8
+#endif
+constexpr int kTriUnrollChain = SPL_TRI_UNROLL_CHAIN;
 constexpr int kChain = SPL_KCHAIN;
 // Chunk length where the summed vector is spread out (the row pass, and
 // column passes whose iterate has sum_j pi_j^2 <= kFineIpr): there 256-row
@@ -121,7 +127,7 @@ __device__ __forceinline__ void chains_flush(float (&in)[kNch][C], float (&acc)[
 // chains (float4 lane e feeds chain e % kNch), which are then added into the
 // compensated outer accumulator: relative rounding error per output about
 // one FP32 unit roundoff instead of ~15 for one sequential 2000-term chain.
-template <int C, int KC = kChain>
+template <int C, int KC = kChain, int UNR = kTriUnroll>
 __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int hi, const float (&m)[C],
                                         float (&acc)[C], float (&comp)[C], int kc = KC) {
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
@@ -135,7 +141,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         float2 in01[C], in23[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) { in01[c] = make_float2(0.f, 0.f); in23[c] = make_float2(0.f, 0.f); }
-#pragma unroll kTriUnroll
+#pragma unroll UNR
         for (int q = 0; q < q1; ++q) {
             const float4 x = v4[(b0 >> 2) + q];
             const float2 xa = make_float2(x.x, x.y), xb = make_float2(x.z, x.w);
@@ -154,7 +160,7 @@ __device__ __forceinline__ void tri_run(const float *__restrict__ v, int lo, int
         const int q1 = (min(hi, b0 + kc) - b0) >> 2;
         float in[kNch][C];
         chains_zero<C>(in);
-#pragma unroll kTriUnroll
+#pragma unroll UNR
         for (int q = 0; q < q1; ++q) {
             const float4 x = v4[(b0 >> 2) + q];
 #pragma unroll
@@ -204,7 +210,8 @@ __device__ __forceinline__ void tri_pass(const float *__restrict__ v, int b_lo, 
             float m[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) m[c] = (below != kRowPass) ? mlo[c] : mhi[c];
-            tri_run<C, KC>(v, below ? b_lo : max(b_lo, span_end), below ? min(b_hi, base) : b_hi, m, acc, comp, kc);
+            tri_run<C, KC, kOneCopy ? kTriUnroll : kTriUnrollChain>(v, below ? b_lo : max(b_lo, span_end),
+                                                                   below ? min(b_hi, base) : b_hi, m, acc, comp, kc);
             return;
         }
         // the span itself (32 C entries, added as chunks of at most kChain)
