@@ -299,7 +299,9 @@ SPL_API spl_status_t spl_batch_stationary_noalloc(const spl_pixel_t *h_pixels, i
  * network changes how many steps are needed, never the accuracy of the
  * result).
  *   spl_mlp_create   : device network for batches of up to max_batch pixels,
- *                      seeded uniform fan-in initialisation; owns its scratch.
+ *                      seeded uniform fan-in initialisation; owns its scratch
+ *                      (device memory, and a pinned host buffer of max_batch
+ *                      pixels through which the pixels are uploaded).
  *   spl_mlp_param_count / set_params / get_params : packed FP32 parameters,
  *                      per layer W (rows x cols, row-major) then b.
  *   spl_mlp_forward  : logits [n][2048] of pixels with n_bins == 2000 (B > 0);

@@ -18,6 +18,8 @@
 #include <numeric>
 #include <vector>
 
+#include "spl_host_pool.h"
+
 #include "spl.h"
 #include "spl_kernels.h"
 
@@ -814,18 +816,37 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
     if (!uniform)
         std::stable_sort(order.begin(), order.end(),
                          [&](int32_t a, int32_t b) { return h_pixels[a].n_bins > h_pixels[b].n_bins; });
-    int nmax = 2;
-    for (int32_t r = 0; r < n; ++r) {
-        const int32_t k = order[r];
-        PixelDev d;
-        spl_status_t st = make_pixel(h_pixels[k], d);
-        if (st != SPL_OK) return st;
-        d.out_off = off[k];
-        d.index = k;
-        ws.h_px[r] = d;
-        nmax = std::max(nmax, (int)d.N);
-    }
-    *nmax_out = nmax;
+    // the per-pixel records, in chunks on the host pool; the error reported is
+    // that of the first bad pixel in work-list order, as a sequential loop
+    // would report it
+    std::atomic<int32_t> bad{n};
+    std::atomic<int> bad_status{SPL_OK};
+    std::atomic<int> nmax{2};
+    std::mutex bad_mu;
+    host_parallel_for(n, 4096, [&](int64_t lo, int64_t hi) {
+        int cmax = 2;
+        for (int64_t r = lo; r < hi; ++r) {
+            const int32_t k = order[r];
+            PixelDev d;
+            const spl_status_t st = make_pixel(h_pixels[k], d);
+            if (st != SPL_OK) {
+                std::lock_guard<std::mutex> g(bad_mu);
+                if ((int32_t)r < bad.load()) {
+                    bad.store((int32_t)r);
+                    bad_status.store(st);
+                }
+                return;
+            }
+            d.out_off = off[k];
+            d.index = k;
+            ws.h_px[r] = d;
+            cmax = std::max(cmax, (int)d.N);
+        }
+        for (int m = nmax.load(); cmax > m && !nmax.compare_exchange_weak(m, cmax);) {
+        }
+    });
+    if (bad.load() < n) return (spl_status_t)bad_status.load();
+    *nmax_out = nmax.load();
     return SPL_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "spl.h"
+#include "spl_host_pool.h"
 #include "spl_kernels.h"
 #include "spl_umma.cuh"
 
@@ -522,6 +523,8 @@ struct spl_mlp {
     size_t warm_cap = 0;
     float *loss = nullptr;     // [M]
     spl_pixel_t *d_px = nullptr;
+    spl_pixel_t *h_stage = nullptr;   // pinned staging of the pixels to upload [max_batch]
+    cudaEvent_t ev_stage = nullptr;   // the last copy out of h_stage
     int *err = nullptr;
     int step = 0;
 };
@@ -543,6 +546,9 @@ void mlp_release(spl_mlp *m) {
     void *p[] = {m->X, m->Xt, m->dZ, m->dZt, m->logits, m->loss, m->d_px, m->err, m->warm};
     for (void *q : p)
         if (q) cudaFree(q);
+    if (m->ev_stage) cudaEventSynchronize(m->ev_stage);
+    if (m->h_stage) cudaFreeHost(m->h_stage);
+    if (m->ev_stage) cudaEventDestroy(m->ev_stage);
     delete m;
 }
 
@@ -654,8 +660,19 @@ spl_status_t backward(spl_mlp *m, int n, const float *d_target) {
     return SPL_OK;
 }
 
+// The caller's pixels (pageable memory) are copied into the pinned staging
+// buffer on the host pool, then sent with one asynchronous copy: a direct
+// copy from pageable memory would hold the host for the driver's own staging
+// while the GPU waits.  The staging buffer is refilled only after its last
+// copy has run.
 spl_status_t upload_pixels(spl_mlp *m, const spl_pixel_t *h_px, int n) {
-    MCU(cudaMemcpyAsync(m->d_px, h_px, sizeof(spl_pixel_t) * n, cudaMemcpyHostToDevice, m->stream));
+    MCU(cudaEventSynchronize(m->ev_stage));
+    spl_pixel_t *dst = m->h_stage;
+    spl::host_parallel_for(n, 4096, [&](int64_t lo, int64_t hi) {
+        std::memcpy(dst + lo, h_px + lo, sizeof(spl_pixel_t) * (size_t)(hi - lo));
+    });
+    MCU(cudaMemcpyAsync(m->d_px, dst, sizeof(spl_pixel_t) * n, cudaMemcpyHostToDevice, m->stream));
+    MCU(cudaEventRecord(m->ev_stage, m->stream));
     return SPL_OK;
 }
 
@@ -707,6 +724,8 @@ extern "C" spl_status_t spl_mlp_create(int32_t max_batch, uint64_t seed, void *s
     chk(dalloc(&m->logits, (size_t)M * kOutPad));
     chk(dalloc(&m->loss, (size_t)M));
     chk(dalloc(&m->d_px, (size_t)M));
+    chk(cudaHostAlloc(reinterpret_cast<void **>(&m->h_stage), sizeof(spl_pixel_t) * (size_t)M, cudaHostAllocDefault));
+    chk(cudaEventCreateWithFlags(&m->ev_stage, cudaEventDisableTiming));
     chk(dalloc(&m->err, 1));
     if (e != cudaSuccess) { mlp_release(m); return e == cudaErrorMemoryAllocation ? SPL_ENOMEM : mfail(e, "alloc"); }
     // Initialisation on the host (uniform fan-in scaling, seeded), zero padding.
