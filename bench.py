@@ -162,6 +162,19 @@ def stored_traffic(arm: str):
     return float(a["dram_bytes_read_per_launch"]) + float(a["dram_bytes_write_per_launch"])
 
 
+def stored_structured_pipes():
+    """Pipe utilisation of the structured (O(N)) batch kernel from the last
+    ncu capture of a 4096-pixel launch (stored beside the traffic figures),
+    or None if the kernel source changed since."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "batch_fused_kernel_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != batch_kernel_source_hash():
+        return None
+    return d.get("structured_pipes")
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -491,6 +504,12 @@ def run_gpu(args):
             lms, lkern = timed_steps(s_learned, args.steps, flush, stream, spl.batch_kernel_ms)
             st["learned"] = {"value": world * n / (statistics.mean(lms) / 1e3), "ms_per_step": statistics.mean(lms),
                              "kernel_ms": statistics.median(lkern), "iters_mean": float(r_sl["iters"].mean())}
+        pipes = stored_structured_pipes()
+        st["roofline"] = None if pipes is None else {
+            "bound": "fp64", "frac": pipes["fp64_pipe_frac"], "unit": "FP64 pipe busy / peak",
+            "fma_pipe_frac": pipes["fma_pipe_frac"], "issue_frac": pipes["issue_frac"],
+            "basis": "ncu on a 4096-pixel launch of this kernel (" + pipes["capture"] + "); no pipe is saturated: "
+                     "the FP64 flux phase keeps the FP64 pipe busiest and the block scans' latency sets the rest"}
         st["note"] = "O(N) scan form of the power step (Eq. 6 triangular structure); same pmfs, not the dense-path number"
         extra["structured"] = st
 
