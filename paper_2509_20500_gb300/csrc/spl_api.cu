@@ -852,8 +852,6 @@ spl_status_t make_work_list(BatchWorkspace &ws, const spl_pixel_t *h_pixels, int
 
 // ---------------------------------------------------------------- batch launch configuration
 //
-// A configuration is the block size (256 or 512 threads), the state level
-// (how many per-pixel vectors live in shared memory) and the blocks per SM.
 // Launch configuration of the batch kernel: block size, columns per thread,
 // state level and blocks per SM.  On the first large batch of a kind (padded
 // N, pass kind, SM count) the feasible configurations are timed on a sample

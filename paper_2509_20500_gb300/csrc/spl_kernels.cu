@@ -1499,10 +1499,10 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
     // windows of this CTA's units, staged as 16-byte async copies into buffer
     // w & 1 (a.chunk rows each, so a window is at most a.chunk / 32 units);
     // unit u holds rows (u mod RB) 32 ... + 31
-    const int kWinUnits = a.chunk / 32;
-    const int nwin = (int)((u1 - u0 + kWinUnits - 1) / kWinUnits);
+    const int win_units = a.chunk / 32;
+    const int nwin = (int)((u1 - u0 + win_units - 1) / win_units);
     auto stage = [&](int w) {
-        const long long wu0 = u0 + (long long)w * kWinUnits, wu1 = min(u1, wu0 + kWinUnits);
+        const long long wu0 = u0 + (long long)w * win_units, wu1 = min(u1, wu0 + win_units);
         const int off0 = (int)(wu0 % RB);
         const int nq = (int)(wu1 - wu0) * 8;
         float *dst = sv + (w & 1) * a.chunk;
@@ -1543,7 +1543,7 @@ __device__ __forceinline__ void chain_run_body(const ChainRunArgs &a, const int 
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const long long wu0 = u0 + (long long)w * kWinUnits, wu1 = min(u1, wu0 + kWinUnits);
+            const long long wu0 = u0 + (long long)w * win_units, wu1 = min(u1, wu0 + win_units);
             const int tw0 = (int)(wu0 / RB);
             const float *wbuf = sv + (w & 1) * a.chunk;
             for (int t = tw0; (long long)t * RB < wu1; ++t) {
@@ -1767,7 +1767,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
     __shared__ StopState s_st[kChainMultiMax];
     __shared__ int s_fin[kChainMultiMax];
     __shared__ int s_tile[6];                           // shared first / last tile: chain, tile, slots
-    const int kWinUnits = m.chunk / 32;   // a staging buffer holds m.chunk rows
+    const int win_units = m.chunk / 32;   // a staging buffer holds m.chunk rows
     __shared__ int s_reg[2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned gen = 0u;
@@ -1828,25 +1828,25 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
         while (s_ub[sl][q + 1] <= u) ++q;
         return q;
     };
-    // windows: at most kWinUnits units of one chain, in unit order
+    // windows: at most win_units units of one chain, in unit order
     auto win_first = [&](int sl, long long u0, long long u1, int &g, long long &lw0, long long &lw1) {
         if (u0 >= u1) return false;
         g = chain_of(sl, u0);
         lw0 = u0 - s_ub[sl][g];
-        lw1 = min(lw0 + kWinUnits, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
+        lw1 = min(lw0 + win_units, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
         return true;
     };
     auto win_next = [&](int sl, long long u1, int &g, long long &lw0, long long &lw1) {
         const long long end = min(u1, s_ub[sl][g + 1]) - s_ub[sl][g];
         if (lw1 < end) {
             lw0 = lw1;
-            lw1 = min(lw0 + kWinUnits, end);
+            lw1 = min(lw0 + win_units, end);
             return true;
         }
         if (s_ub[sl][g + 1] >= u1) return false;
         g = chain_of(sl, s_ub[sl][g + 1]);
         lw0 = 0;
-        lw1 = min((long long)kWinUnits, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
+        lw1 = min((long long)win_units, min(u1, s_ub[sl][g + 1]) - s_ub[sl][g]);
         return true;
     };
     // 16-byte async copies of a window's rows into buffer buf; step k reads
