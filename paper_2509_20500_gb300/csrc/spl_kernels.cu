@@ -1689,10 +1689,12 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_run_kernel(ChainRunArgs a) {
 // evenly over the CTAs, each CTA leaves one partial per tile it touches and
 // the last CTA to finish a shared tile adds them in CTA order; after one grid
 // barrier the active chains' bins, chain after chain, are split evenly over
-// the CTAs for the normalisation.  Every CTA keeps an identical copy of each
-// chain's stop state and takes the same decisions (on step k - 1, one pass
-// after it, as the single-chain kernel), so all CTAs drop a chain at the same
-// step and re-split the work of the others.
+// the CTAs for the normalisation.  A second barrier publishes every CTA's
+// step statistics; every CTA keeps an identical copy of each chain's stop
+// state and decides on step k right then (the single-chain kernel decides one
+// pass later instead, to save the barrier; here a pass is worth more than a
+// barrier), so all CTAs drop a chain at the same step and re-split the work
+// of the others, and no chain runs a pass past the step that ends it.
 
 __device__ __forceinline__ long long lk_owner(long long u, long long U, int G) {
     return ((u + 1) * G + U - 1) / U - 1;
@@ -2000,10 +2002,7 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
             }
             return;
         }
-        // ---- step k is complete: per chain (one warp each) the sum of y and,
-        // from the statistics the CTAs left in step k - 1's normalisation, the
-        // decision on step k - 1
-        const int pk = (k + 2) % 3;
+        // ---- step k is complete: per chain (one warp each) the sum of y
         for (int q = wid; q < n; q += kRunW) {
             if (!(mask >> q & 1u)) continue;
             const ChainRunArgs &c = cc[q];
@@ -2018,32 +2017,85 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
                 sy += (x0 + x1) + (x2 + x3);
             }
             sy = warp_sum(sy);
-            float sx = 0.f, sd = 0.f, s1 = 0.f, s2 = 0.f;
-            if (k >= 2) {
-                const long long NB = s_nb[pk][n], j0 = s_nb[pk][q];
-                const int GeN = (int)min((long long)G, NB);
-                const int bF = (int)lk_owner(j0, NB, GeN), bL = (int)lk_owner(j0 + c.N - 1, NB, GeN);
-                const float4 *bs = reinterpret_cast<const float4 *>(c.blk + (size_t)((k - 1) & 1) * G * 4);
-                for (int i = bF + lane; i <= bL; i += 32) {
-                    const float4 x = __ldcg(bs + i);
-                    sx += x.x;
-                    sd += x.y;
-                    s1 += x.z;
-                    s2 += x.w;
+            if (lane == 0) s_inv[q] = 1.f / sy;
+        }
+        __syncthreads();
+        // ---- normalise step k over this CTA's bins of the chains in the pass,
+        // leaving this CTA's step statistics of each chain in blk
+        const long long NB = s_nb[sl][n];
+        const int GeN = (int)min((long long)G, NB);
+        const long long j0 = b < GeN ? (long long)b * NB / GeN : 0, j1 = b < GeN ? (long long)(b + 1) * NB / GeN : 0;
+        {
+            int piece = 0;
+            for (int q = 0; q < n; ++q) {
+                if (!(mask >> q & 1u)) continue;
+                const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
+                if (cb1 <= j0 || cb0 >= j1) continue;
+                const ChainRunArgs &c = cc[q];
+                const int a0 = (int)(max(j0, cb0) - cb0), a1 = (int)(min(j1, cb1) - cb0);
+                float *pcur = (k & 1) ? c.pi_alt : c.pi;
+                const float *pprev = (k & 1) ? c.pi : c.pi_alt;
+                const float *yk = c.y + (size_t)(k & 1) * c.vlen;
+                const float inv = s_inv[q];
+                float stats[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int j = a0 + tid; j < a1; j += kRunNT) {
+                    const float pn = __ldcg(yk + j) * inv;
+                    // written by whichever CTA held bin j in the last step (L2 loads)
+                    const float d = pn - __ldcg(pprev + j);
+                    const float f1 = __ldcg(c.d1 + j);
+                    stats[0] += fabsf(d);
+                    stats[1] = fmaf(d, d, stats[1]);
+                    stats[2] = fmaf(d, f1, stats[2]);
+                    stats[3] = fmaf(d, __ldcg(c.d2 + j), stats[3]);
+                    c.d2[j] = f1;
+                    c.d1[j] = d;
+                    pcur[j] = pn;
                 }
-                sx = warp_sum(sx);
-                sd = warp_sum(sd);
-                s1 = warp_sum(s1);
-                s2 = warp_sum(s2);
+                // one barrier; consecutive chains alternate buffers, so a buffer
+                // is rewritten only after every thread passed the barrier between
+                block_sum_k_1bar<kRunNT, 4>(stats, red + (piece++ & 1) * 4 * kRunW);
+                if (tid == 0)
+                    reinterpret_cast<float4 *>(c.blk + (size_t)(k & 1) * G * 4)[b] =
+                        make_float4(stats[0], stats[1], stats[2], stats[3]);
             }
-            if (lane == 0) {
-                s_inv[q] = 1.f / sy;
-                int fin = 0;
-                if (k >= 2) {
-                    const int su = stop_update(s_st[q], sx, sd, s1, s2, m.tol_err, m.min_iter);
-                    if (su != STOP_CONTINUE) fin = su == STOP_CONVERGED ? 1 : 2;
-                    else if (s_st[q].k >= m.max_iter) fin = 2;
+        }
+        // ---- every CTA's statistics of step k are written: one more barrier,
+        // then the decision on step k itself (no pass is run past it)
+        if (!grid_sync(sbar, gen, cc[0].err_flag, &s_flag, b, G)) {
+            if (tid < n) {
+                *cc[tid].err_flag = 1;
+                if (b == 0) {
+                    ChainState *stp = cc[tid].state;
+                    stp->st = s_st[tid];
+                    stp->done = 1;
+                    stp->status = ST_ENOCONV;
                 }
+            }
+            return;
+        }
+        for (int q = wid; q < n; q += kRunW) {
+            if (!(mask >> q & 1u)) continue;
+            const ChainRunArgs &c = cc[q];
+            const long long cj0 = s_nb[sl][q];
+            const int bF = (int)lk_owner(cj0, NB, GeN), bL = (int)lk_owner(cj0 + c.N - 1, NB, GeN);
+            const float4 *bs = reinterpret_cast<const float4 *>(c.blk + (size_t)(k & 1) * G * 4);
+            float sx = 0.f, sd = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int i = bF + lane; i <= bL; i += 32) {
+                const float4 x = __ldcg(bs + i);
+                sx += x.x;
+                sd += x.y;
+                s1 += x.z;
+                s2 += x.w;
+            }
+            sx = warp_sum(sx);
+            sd = warp_sum(sd);
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                int fin = 0;
+                const int su = stop_update(s_st[q], sx, sd, s1, s2, m.tol_err, m.min_iter);
+                if (su != STOP_CONTINUE) fin = su == STOP_CONVERGED ? 1 : 2;
+                else if (s_st[q].k >= m.max_iter) fin = 2;
                 s_fin[q] = fin;
             }
         }
@@ -2057,65 +2109,28 @@ __global__ void __launch_bounds__(kRunNT, 2) chain_multi_kernel(const __grid_con
             stp->done = 1;
             stp->status = s_fin[tid] == 1 ? ST_OK : ST_ENOCONV;
         }
-        // the next step's partition, and its first window staged while this
-        // step is normalised
-        if (next) {
-            if (tid == 0) bases((k + 1) % 3, next);
-            __syncthreads();
+        // a chain decided on step k keeps pi^(k); when it lives in pi_alt (k
+        // odd), the CTA that normalised a bin copies it
+        if (k & 1) {
+            for (int q = 0; q < n; ++q) {
+                if (!(mask >> q & 1u) || !s_fin[q]) continue;
+                const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
+                if (cb1 <= j0 || cb0 >= j1) continue;
+                const ChainRunArgs &c = cc[q];
+                const int a0 = (int)(max(j0, cb0) - cb0), a1 = (int)(min(j1, cb1) - cb0);
+                for (int j = a0 + tid; j < a1; j += kRunNT) c.pi[j] = c.pi_alt[j];
+            }
+        }
+        if (!next) return;   // every chain decided
+        // the next step's partition, and its first window staged
+        if (tid == 0) bases((k + 1) % 3, next);
+        __syncthreads();
+        {
             long long v0, v1, w0, w1;
             int q;
             range((k + 1) % 3, v0, v1);
             if (win_first((k + 1) % 3, v0, v1, q, w0, w1)) stage(q, w0, w1, 0, k + 1);
         }
-        // ---- normalise step k over this CTA's bins of the chains in the pass;
-        // a chain decided on step k - 1 instead keeps pi^(k-1) as its result
-        {
-            const long long NB = s_nb[sl][n];
-            const int GeN = (int)min((long long)G, NB);
-            if (b < GeN) {
-                const long long j0 = (long long)b * NB / GeN, j1 = (long long)(b + 1) * NB / GeN;
-                int piece = 0;
-                for (int q = 0; q < n; ++q) {
-                    if (!(mask >> q & 1u)) continue;
-                    const long long cb0 = s_nb[sl][q], cb1 = s_nb[sl][q + 1];
-                    if (cb1 <= j0 || cb0 >= j1) continue;
-                    const ChainRunArgs &c = cc[q];
-                    const int a0 = (int)(max(j0, cb0) - cb0), a1 = (int)(min(j1, cb1) - cb0);
-                    if (s_fin[q]) {
-                        // pi^(k-1) is the result; it lives in pi_alt when k-1 is odd
-                        if ((k - 1) & 1)
-                            for (int j = a0 + tid; j < a1; j += kRunNT) c.pi[j] = __ldcg(c.pi_alt + j);
-                        continue;
-                    }
-                    float *pcur = (k & 1) ? c.pi_alt : c.pi;
-                    const float *pprev = (k & 1) ? c.pi : c.pi_alt;
-                    const float *yk = c.y + (size_t)(k & 1) * c.vlen;
-                    const float inv = s_inv[q];
-                    float stats[4] = {0.f, 0.f, 0.f, 0.f};
-                    for (int j = a0 + tid; j < a1; j += kRunNT) {
-                        const float pn = __ldcg(yk + j) * inv;
-                        // written by whichever CTA held bin j in the last step (L2 loads)
-                        const float d = pn - __ldcg(pprev + j);
-                        const float f1 = __ldcg(c.d1 + j);
-                        stats[0] += fabsf(d);
-                        stats[1] = fmaf(d, d, stats[1]);
-                        stats[2] = fmaf(d, f1, stats[2]);
-                        stats[3] = fmaf(d, __ldcg(c.d2 + j), stats[3]);
-                        c.d2[j] = f1;
-                        c.d1[j] = d;
-                        pcur[j] = pn;
-                    }
-                    // one barrier; consecutive chains alternate buffers, so a buffer
-                    // is rewritten only after every thread passed the barrier between
-                    block_sum_k_1bar<kRunNT, 4>(stats, red + (piece++ & 1) * 4 * kRunW);
-                    if (tid == 0)
-                        reinterpret_cast<float4 *>(c.blk + (size_t)(k & 1) * G * 4)[b] =
-                            make_float4(stats[0], stats[1], stats[2], stats[3]);
-                }
-            }
-        }
-        if (!next) return;   // every chain decided (no window was staged)
-        __syncthreads();
     }
 }
 
