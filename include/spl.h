@@ -32,7 +32,10 @@
  *    threads (they run one at a time; spl_batch_stationary_noalloc shares one
  *    static scratch area instead, see there).  A chain (spl_chain_t) or a
  *    network (spl_mlp_t) is used by one thread at a time; distinct objects are
- *    independent.
+ *    independent.  The per-pixel host work of a large batch call runs on a
+ *    small pool of library threads (up to 7, started on the first such call,
+ *    idle between calls, never joined); in a process forked after they
+ *    started, that work runs on the calling thread.
  */
 #ifndef SPL_H
 #define SPL_H
