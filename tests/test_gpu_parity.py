@@ -632,6 +632,23 @@ def test_batch_invalid_pixel_rejected(spl):
     assert ei.value.status == spl.SPL_EINVAL
 
 
+def test_batch_invalid_pixels_in_a_large_batch_rejected(spl):
+    """A batch large enough that its work list is built in several chunks on
+    host threads: bad pixels in two different chunks give SPL_EINVAL before
+    anything is launched, and the next valid call on the same workspace still
+    gives the same pmfs as before."""
+    px = W.array_pixels(20000, seed=18, n_bins=100)
+    ref, off, _ = spl.batch_stationary(px[:50])
+    bad = px.copy()
+    bad["sigma"][15000] = -1.0
+    bad["t_r"][3000] = 0.0
+    with pytest.raises(spl.SplError) as ei:
+        spl.batch_stationary(bad)
+    assert ei.value.status == spl.SPL_EINVAL
+    again, _, _ = spl.batch_stationary(px[:50])
+    np.testing.assert_array_equal(again.cpu().numpy(), ref.cpu().numpy())
+
+
 def test_batch_empty(spl):
     px = W.array_pixels(0, seed=1)
     out, off, reps = spl.batch_stationary(px, out=torch.empty(1, device="cuda"))
